@@ -1,0 +1,189 @@
+"""FP64 CPU oracle for the softened gravitational force and potential.
+
+TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use this package. The product path (the CUDA
+library and its Python binding) never imports it.
+
+The arithmetic lives in ``nb_oracle.c`` (plain double loops, see its header);
+this module compiles it with gcc and exposes it through ctypes on numpy
+float64 arrays. Inputs given as FP32 are promoted exactly to FP64.
+
+Functions, each following the paper (Fujiwara & Nakasato, arXiv:0904.3659):
+  force        Eq. (gravity), Section "Introduction": a_i, p_i for all i
+  force_rows   Eq. (gravity) for a sampled list of i
+  force_vjp    chain rule of Eq. (gravity): dL/dx, dL/dm for
+               L = sum_i ga_i . a_i + gp_i p_i
+  leapfrog     Eqs. (1)-(3), Section "Method", with the physical sign g = -a
+  energy       K = 1/2 sum m v^2, W = -1/2 sum m p
+
+Parity status: every function is pinned by CPU tests against closed forms,
+exact scaling laws, invariants, finite differences and high-precision brute
+force (tests/test_oracle_*.py); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nb_oracle.c")
+_LIB = os.path.join(_HERE, "libnb_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_CFLAGS = ["-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile nb_oracle.c into libnb_oracle.so next to it (gcc, no CUDA)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.nbo_num_threads.restype = ctypes.c_int
+            lib.nbo_set_num_threads.argtypes = [ctypes.c_int]
+            lib.nbo_force.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D, _D]
+            lib.nbo_force_rows.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double,
+                                           ctypes.c_int64, _I64, _D, _D, _D]
+            lib.nbo_force_vjp.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double,
+                                          _D, _D, _D, _D]
+            lib.nbo_force_vjp_rows.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double,
+                                               _D, _D, ctypes.c_int64, _I64, _D, _D]
+            lib.nbo_leapfrog.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int64, _D, _D]
+            lib.nbo_energy.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, _D, _D]
+            _lib = lib
+    return _lib
+
+
+def _f64(a, shape=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        arr = arr.reshape(shape)
+    return arr
+
+
+def _p(arr):
+    return arr.ctypes.data_as(_D)
+
+
+def num_threads() -> int:
+    return int(_load().nbo_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    _load().nbo_set_num_threads(int(n))
+
+
+def _eps64(eps) -> float:
+    # The CUDA library takes eps as FP32; the oracle uses that same FP32
+    # value, promoted exactly to FP64 (eps^2 is then formed in FP64).
+    return float(np.float32(eps))
+
+
+def force(x, m, eps):
+    """Eq. (gravity) for all particles. Returns (a [n,3], p [n], amag [n])."""
+    x = _f64(x)
+    n = x.shape[0]
+    x = x.reshape(n, 3)
+    m = _f64(m, (n,))
+    a = np.zeros((n, 3))
+    p = np.zeros(n)
+    amag = np.zeros(n)
+    if n:
+        _load().nbo_force(n, _p(x), _p(m), _eps64(eps), _p(a), _p(p), _p(amag))
+    return a, p, amag
+
+
+def force_rows(x, m, eps, rows):
+    """Eq. (gravity) for the particles listed in rows."""
+    x = _f64(x)
+    n = x.shape[0]
+    x = x.reshape(n, 3)
+    m = _f64(m, (n,))
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    if rows.size and (rows.min() < 0 or rows.max() >= n):
+        raise IndexError("row out of range")
+    k = rows.size
+    a = np.zeros((k, 3))
+    p = np.zeros(k)
+    amag = np.zeros(k)
+    if k:
+        _load().nbo_force_rows(n, _p(x), _p(m), _eps64(eps), k,
+                               rows.ctypes.data_as(_I64), _p(a), _p(p), _p(amag))
+    return a, p, amag
+
+
+def force_vjp(x, m, eps, ga, gp, rows=None):
+    """dL/dx, dL/dm of L = sum ga.a + gp p (all rows, or the listed ones)."""
+    x = _f64(x)
+    n = x.shape[0]
+    x = x.reshape(n, 3)
+    m = _f64(m, (n,))
+    ga = _f64(ga, (n, 3))
+    gp = _f64(gp, (n,))
+    lib = _load()
+    if rows is None:
+        gx = np.zeros((n, 3))
+        gm = np.zeros(n)
+        if n:
+            lib.nbo_force_vjp(n, _p(x), _p(m), _eps64(eps), _p(ga), _p(gp), _p(gx), _p(gm))
+        return gx, gm
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    k = rows.size
+    gx = np.zeros((k, 3))
+    gm = np.zeros(k)
+    if k:
+        lib.nbo_force_vjp_rows(n, _p(x), _p(m), _eps64(eps), _p(ga), _p(gp), k,
+                               rows.ctypes.data_as(_I64), _p(gx), _p(gm))
+    return gx, gm
+
+
+def leapfrog(x, v, m, eps, dt, nsteps):
+    """Eqs. (1)-(3) for nsteps steps. Returns (x, v, g) after the last step,
+    g the physical acceleration -a at the final positions."""
+    x = _f64(x).copy()
+    n = x.shape[0]
+    x = x.reshape(n, 3)
+    v = _f64(v, (n, 3)).copy()
+    m = _f64(m, (n,))
+    g = np.zeros((n, 3))
+    work = np.zeros(4 * max(n, 1))
+    if n:
+        _load().nbo_leapfrog(n, _p(x), _p(v), _p(m), _eps64(eps), float(dt),
+                             int(nsteps), _p(g), _p(work))
+    return x, v, g
+
+
+def energy(x, v, m, eps):
+    """Returns (K, W): kinetic and potential energy, W = -1/2 sum m p."""
+    x = _f64(x)
+    n = x.shape[0]
+    x = x.reshape(n, 3)
+    v = _f64(v, (n, 3))
+    m = _f64(m, (n,))
+    out = np.zeros(2)
+    work = np.zeros(4 * max(n, 1))
+    if n:
+        _load().nbo_energy(n, _p(x), _p(v), _p(m), _eps64(eps), _p(out), _p(work))
+    return float(out[0]), float(out[1])
