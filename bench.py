@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the direct-summation gravity path on GB300.
+
+One step = one nb_force call (pack -> pair kernel -> combine) evaluating
+Eq. (gravity) (Fujiwara & Nakasato, arXiv:0904.3659) for a Plummer sphere of
+N = 2^20 particles, eps = 1/256, FP32, inputs resident in HBM. The headline
+value is interactions per second (N^2 per step, the paper's convention) of
+the plain path; the compensated path is timed right after it on the same
+inputs. Gflop/s are also given at the paper's 38 flop per interaction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the same workload
+(the computation needs no exchange), so scaling is weak and the value is the
+sum over ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of rows of the
+same workload on the host cores (the reference arm for this project; the
+paper's own RV770/CAL code is not available).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "plummer1m"
+FLOP_PER_INT_PAPER = 38          # the paper's convention (Section "Experiments")
+FP32_OPS_PER_INT = 16            # FP32 pipe operations per interaction in our kernel
+FP32_LANES_PER_SM = 128          # FP32 lanes per SM per clock
+MUFU_PER_INT = 1
+
+
+# --------------------------------------------------------------------------
+# host-side helpers (no GPU needed; covered by tests/test_bench_host.py)
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(per_rank_units: float, world: int, ms_per_step_max: float) -> float:
+    """Whole-job rate: units all ranks processed per second of the slowest rank."""
+    return per_rank_units * world / (ms_per_step_max * 1e-3)
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int = 0, period_ms: int = 200):
+        self.gpu_index = gpu_index
+        self.period_ms = period_ms
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", f"-lms={self.period_ms}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self._t is not None:
+                self._t.join(timeout=2)
+
+    def summary(self):
+        return summarize_clocks(self.lines)
+
+
+def summarize_clocks(lines):
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [s.strip() for s in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for k, nm in enumerate(names):
+            if f[5 + k].lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    # Under load: samples above 30% of max (the first/last samples can be idle).
+    top = max(smax) if smax else max(sm)
+    loaded = [v for v in sm if v > 0.3 * top] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": top,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+# inputs
+
+def make_inputs(n, seed):
+    x, _, m = workloads.plummer(n, seed=seed)
+    return np.ascontiguousarray(x.astype(np.float32)), np.ascontiguousarray(m.astype(np.float32))
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of rows
+
+def cpu_oracle_rate(x32, m32, eps, target_s=12.0, rows_seed=2, min_rows=64,
+                    extra_rows=None):
+    """Time oracle.force_rows on a sample of rows sized for about target_s
+    seconds. Returns (rate in interactions/s, dict describing the sample,
+    oracle results for extra_rows if given)."""
+    import oracle
+    n = x32.shape[0]
+    cores = oracle.num_threads()
+    rows = workloads.sample_rows(n, min_rows, seed=rows_seed + 1000)
+    t0 = time.perf_counter()
+    oracle.force_rows(x32, m32, eps, rows)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(n, max(min_rows, min_rows * target_s / dt)))
+    rows = workloads.sample_rows(n, k, seed=rows_seed + 1000)
+    t0 = time.perf_counter()
+    oracle.force_rows(x32, m32, eps, rows)
+    dt = time.perf_counter() - t0
+    rate = k * n / dt
+    extra = None
+    if extra_rows is not None:
+        extra = oracle.force_rows(x32, m32, eps, extra_rows)
+    return rate, {"rows": int(k), "n": int(n), "seconds": dt, "cores": cores}, extra
+
+
+def oracle_errors(a, p, ref):
+    ra, rp, ramag = ref
+    ea = np.linalg.norm(a.astype(np.float64) - ra, axis=1) / ramag
+    ep = np.abs(p.astype(np.float64) - rp) / rp
+    return {"max_rel_a": float(ea.max()), "max_rel_p": float(ep.max()),
+            "median_rel_a": float(np.median(ea)), "median_rel_p": float(np.median(ep))}
+
+
+# --------------------------------------------------------------------------
+# our arm
+
+def run_ours(args):
+    import torch
+    import paper_0904_3659_gb300 as nb
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    w = workloads.WORKLOADS[WORKLOAD]
+    n, eps = w["n"], np.float32(w["eps"])
+    x32, m32 = make_inputs(n, w["seed"])
+    xt = torch.from_numpy(x32).to(dev)
+    mt = torch.from_numpy(m32).to(dev)
+    a = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    p = torch.empty((n,), dtype=torch.float32, device=dev)
+    ctx = nb.Context(dev.index)
+    stream = torch.cuda.current_stream(dev)
+
+    # Tile choice: tune on a quarter-size proxy (same inner loop; the
+    # persistent split balances the full size), then fix it.
+    tiles = {}
+    for mode in (nb.NB_PLAIN, nb.NB_COMPENSATED):
+        if args.tile_tune:
+            t, _ = nb.nb_autotune(ctx, n // 4, mode)
+            nb.nb_set_tile(ctx, mode, t)
+        tiles[mode] = nb.nb_get_tile(ctx, n, mode)
+        nb.nb_reserve(ctx, n, mode)
+
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def timed(mode, steps, warmup):
+        for _ in range(warmup):
+            nb.nb_force(ctx, xt, mt, n, eps, a, p, mode, stream)
+        nb.nb_synchronize(ctx, stream)
+        nb.nb_timing_enable(ctx, True)
+        nb.nb_timing_reset(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush_buf.fill_(float(k))          # L2 flush between timed steps (untimed)
+            ev[k][0].record(stream)
+            nb.nb_force(ctx, xt, mt, n, eps, a, p, mode, stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        nb.nb_synchronize(ctx, stream)
+        step_ms = [s.elapsed_time(e) for s, e in ev]
+        kernels = {name: nb.nb_timing_read(ctx, kid) for name, kid in
+                   (("pack", nb.KERNEL_PACK), ("pair", nb.KERNEL_PAIR),
+                    ("combine", nb.KERNEL_REDUCE))}
+        nb.nb_timing_enable(ctx, False)
+        return step_ms, kernels
+
+    with ClockSampler(dev.index) as clk:
+        plain_ms, plain_k = timed(nb.NB_PLAIN, args.steps, args.warmup)
+        a_plain = a.cpu().numpy()
+        p_plain = p.cpu().numpy()
+        comp_ms, comp_k = timed(nb.NB_COMPENSATED, args.steps, args.warmup)
+        a_comp = a.cpu().numpy()
+        p_comp = p.cpu().numpy()
+    clocks = clk.summary()
+
+    ms_plain = max_over_ranks(sum(plain_ms) / len(plain_ms), world)
+    ms_comp = max_over_ranks(sum(comp_ms) / len(comp_ms), world)
+    interactions = float(n) * float(n)
+    value = aggregate(interactions, world, ms_plain)
+    value_comp = aggregate(interactions, world, ms_comp)
+
+    # End to end through the public C ABI with host buffers (pinned), copies
+    # inside the timed region.
+    hx = torch.from_numpy(x32).pin_memory()
+    hm = torch.from_numpy(m32).pin_memory()
+    ha = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    hp = torch.empty((n,), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, min(args.warmup, 2))):
+        nb.nb_force_host(ctx, hx.data_ptr(), hm.data_ptr(), n, eps, ha.data_ptr(), hp.data_ptr(),
+                         nb.NB_PLAIN, stream)
+    barrier(world)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t0 = time.perf_counter()
+        nb.nb_force_host(ctx, hx.data_ptr(), hm.data_ptr(), n, eps, ha.data_ptr(), hp.data_ptr(),
+                         nb.NB_PLAIN, stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    barrier(world)
+    e2e_ms_max = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
+
+    # Roofline of the dominant kernel (the pair kernel): FP32 pipe bound.
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = (peaks or {}).get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    pair_ms_total, pair_launches = plain_k["pair"]
+    pair_ms = pair_ms_total / max(pair_launches, 1)
+    achieved = interactions / (pair_ms * 1e-3) / 1e9                     # G-int/s
+    peak = sm_count * sm_max_mhz * 1e6 * FP32_LANES_PER_SM / FP32_OPS_PER_INT / 1e9
+    peak17 = sm_count * sm_max_mhz * 1e6 * FP32_LANES_PER_SM / 17 / 1e9
+    comp_pair_ms = comp_k["pair"][0] / max(comp_k["pair"][1], 1)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return None
+
+    out = {
+        "metric": "G-interactions/s and % FP32/MUFU roofline at N=2^20 vs FP64-oracle error",
+        "value": value / 1e9,
+        "unit": "G-int/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_plain,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic Plummer sphere (seed 0), float32",
+        "config": {"workload": WORKLOAD, "n": n, "eps": float(eps), "mode": "plain",
+                   "tile": list(tiles[nb.NB_PLAIN].as_tuple()),
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "gflops_38": value * FLOP_PER_INT_PAPER / 1e9,
+        "compensated": {"value": value_comp / 1e9, "unit": "G-int/s", "ms_per_step": ms_comp,
+                        "slowdown_vs_plain": ms_comp / ms_plain,
+                        "tile": list(tiles[nb.NB_COMPENSATED].as_tuple()),
+                        "pair_ms": comp_pair_ms},
+        "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in plain_k.items()},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G-int/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "basis": (f"{sm_count} SMs x {sm_max_mhz:.0f} MHz x {FP32_LANES_PER_SM} FP32 "
+                               f"lanes / {FP32_OPS_PER_INT} FP32 ops per interaction "
+                               f"(+{MUFU_PER_INT} MUFU rsqrt, not binding); sm_max_mhz of "
+                               f"{'measured' if peaks else 'nvidia-smi'} peaks"),
+                     "frac_17op_convention": achieved / peak17},
+        "e2e": {"value": interactions * world / (e2e_ms_max * 1e-3) / 1e9, "unit": "G-int/s",
+                "h2d_bytes_per_step": int(x32.nbytes + m32.nbytes),
+                "d2h_bytes_per_step": int(4 * n * 3 + 4 * n)},
+        "gpu_launches": 3 * args.steps * 2,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        rows = workloads.sample_rows(n, w["sample"], w["sample_seed"])
+        rate, sample, ref = cpu_oracle_rate(x32, m32, eps, target_s=args.cpu_seconds,
+                                            extra_rows=rows)
+        out["cpu_baseline"] = {"value": rate / 1e9, "unit": "G-int/s", "cores": sample["cores"],
+                               "kind": "oracle",
+                               "sample": (f"{sample['rows']} random rows x all {n} j of the same "
+                                          f"workload, FP64, {sample['seconds']:.1f} s")}
+        out["oracle_error"] = {"rows": int(rows.size),
+                               "plain": oracle_errors(a_plain[rows], p_plain[rows], ref),
+                               "compensated": oracle_errors(a_comp[rows], p_comp[rows], ref)}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    w = workloads.WORKLOADS[WORKLOAD]
+    n, eps = w["n"], np.float32(w["eps"])
+    x32, m32 = make_inputs(n, w["seed"])
+    cores = oracle.num_threads()
+    # Rows per step sized for about two seconds of oracle work.
+    probe = workloads.sample_rows(n, 32, seed=11)
+    t0 = time.perf_counter()
+    oracle.force_rows(x32, m32, eps, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    k = int(max(32, min(n, 32 * 2.0 / dt)))
+    times = []
+    for step in range(args.warmup + args.steps):
+        rows = workloads.sample_rows(n, k, seed=100 + step)
+        t0 = time.perf_counter()
+        oracle.force_rows(x32, m32, eps, rows)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = k * n / (ms * 1e-3) / 1e9
+    out = {
+        "impl": "reference",
+        "metric": "G-interactions/s and % FP32/MUFU roofline at N=2^20 vs FP64-oracle error",
+        "value": value, "unit": "G-int/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic Plummer sphere (seed 0), float32",
+        "config": {"workload": WORKLOAD, "n": n, "eps": float(eps),
+                   "sample_rows_per_step": k},
+        "cpu_baseline": {"value": value, "unit": "G-int/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{k} random rows x all {n} j per step, FP64"},
+        "e2e": {"value": value, "unit": "G-int/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tile-tune", dest="tile_tune", action="store_false")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

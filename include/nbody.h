@@ -1,0 +1,224 @@
+/*
+ * nbody.h -- C ABI of the GB300 (sm_103a) direct-summation gravity library.
+ *
+ * The library computes the exact softened gravitational acceleration and
+ * potential of N particles, Eq. (gravity) of Fujiwara & Nakasato, "Fast
+ * Simulations of Gravitational Many-body Problem on RV770 GPU"
+ * (arXiv:0904.3659), Section "Introduction":
+ *
+ *     a_i = sum_{j != i} m_j (x_i - x_j) / (|x_i - x_j|^2 + eps^2)^{3/2}
+ *     p_i = sum_{j != i} m_j / (|x_i - x_j|^2 + eps^2)^{1/2}
+ *
+ * and, around it, the leap-frog integrator of Section "Method", Eqs. (1)-(3).
+ *
+ * Conventions shared by every entry point:
+ *  - Sign: a and p are returned exactly as printed in Eq. (gravity): a_i
+ *    points away from the other masses and p_i > 0 (G = 1). The physical
+ *    gravitational acceleration is -a_i and the potential energy is
+ *    W = -1/2 sum_i m_i p_i. nb_leapfrog_step applies that physical sign.
+ *  - The j == i term is left out by index; distinct particles at the same
+ *    position are summed (0 to a, m_j/eps to p).
+ *  - Layout: positions and accelerations are row-major [n][3] arrays
+ *    (x0,y0,z0,x1,...), masses and potentials are [n]. Unless an entry point
+ *    says otherwise, every array argument is a DEVICE pointer on the device
+ *    the context was created for. The caller owns every data buffer; the
+ *    context owns only scratch memory, events and the tuning table.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream). Calls enqueue work on it and return without waiting,
+ *    except where stated. Device-side errors (a bounded wait that ran out)
+ *    are reported by the next nb_synchronize on that context.
+ *  - Errors: every call returns an nb_status. NB_OK on success; on failure
+ *    nothing is enqueued, output buffers are untouched, and nb_last_error()
+ *    gives a one-line message. n == 0 is a valid no-op. A negative count, a
+ *    NULL pointer where data is needed, or eps not finite or not > 0
+ *    (the paper's eps exists to prevent division by zero) is NB_ERR_ARG.
+ *    Non-finite positions or masses are not checked; they propagate.
+ *  - Contexts are not thread-safe: use one per host thread.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nb_status {
+    NB_OK = 0,
+    NB_ERR_ARG = 1,              /* invalid argument; nothing was done */
+    NB_ERR_CUDA = 2,             /* a CUDA runtime call or launch failed */
+    NB_ERR_OOM = 3,              /* scratch allocation failed */
+    NB_ERR_TIMEOUT = 4,          /* a bounded device wait ran out (results invalid) */
+    NB_ERR_NOT_IMPLEMENTED = 5   /* entry point present but not built */
+} nb_status;
+
+/*
+ * Arithmetic variants of the pair kernel. Both keep every pair interaction in
+ * FP32 (x_i - x_j, s, rsqrt on the special-function unit plus one
+ * Newton-Raphson step, products) and add results in FP32.
+ *  NB_PLAIN        two-level blocked sum: a register partial per j-tile, then
+ *                  a running sum across tiles. Target: max per-particle
+ *                  relative error <= 1e-5 against FP64.
+ *  NB_COMPENSATED  the tile partials enter the running sum through Kahan
+ *                  compensation, the cross-block combine is compensated too,
+ *                  and positions held in FP64 (leap-frog state) enter the
+ *                  pair arithmetic as FP32 offsets from a per-tile reference
+ *                  point. Target: <= 1e-6.
+ */
+typedef enum nb_mode { NB_PLAIN = 0, NB_COMPENSATED = 1 } nb_mode;
+
+typedef struct nb_ctx nb_ctx;
+
+/* Tile shape of the pair kernel: `threads` per CTA, `ipt` i-particles per
+ * thread held in registers (even: they are processed in packed FP32 pairs),
+ * `jtile` j-particles per shared-memory stage, `stages` stages in flight. */
+typedef struct nb_tile {
+    int threads;
+    int ipt;
+    int jtile;
+    int stages;
+} nb_tile;
+
+/* Create a context on CUDA device `device`. *out receives the handle. */
+nb_status nb_create(nb_ctx **out, int device);
+
+/* Free the context's scratch, events and streams. NULL is ignored. Waits
+ * for the device work the context enqueued to finish. */
+void nb_destroy(nb_ctx *ctx);
+
+/* Message describing the last failure on this context ("" if none). The
+ * pointer stays valid until the next call on the context. NULL ctx gives the
+ * message of the last failed nb_create. */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Static name of a status code. */
+const char *nb_status_string(nb_status s);
+
+/*
+ * Eq. (gravity) for all n particles.
+ *   x    [n][3] FP32 device, positions
+ *   m    [n]    FP32 device, masses
+ *   eps  softening (> 0, finite)
+ *   a    [n][3] FP32 device, output accelerations (literal sign)
+ *   p    [n]    FP32 device, output potentials (positive)
+ * x/m must not overlap a/p. Asynchronous on `stream`. The first call at a
+ * larger n than before (or in a new mode) allocates scratch (cudaMalloc,
+ * which synchronises the device); nb_reserve does that ahead of time.
+ * Results are bit-for-bit reproducible for a fixed (n, mode, tile, device).
+ */
+nb_status nb_force(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
+                   float *a, float *p, nb_mode mode, void *stream);
+
+/*
+ * nb_force on HOST buffers: copies x and m to the device, runs nb_force,
+ * copies a and p back and waits for the copies to finish. Same argument
+ * meaning as nb_force, but all four arrays are host memory (pinned memory
+ * gives the fastest copies). Device staging buffers are owned by ctx.
+ */
+nb_status nb_force_host(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
+                        float *a, float *p, nb_mode mode, void *stream);
+
+/* Allocate the scratch nb_force needs for up to n particles in `mode`, so
+ * that later calls up to that size allocate nothing. */
+nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode);
+
+/*
+ * Many independent systems in one launch (Eq. (gravity) within each cluster,
+ * no interaction between clusters).
+ *   x, m, a, p    as in nb_force, clusters concatenated
+ *   offsets       [n_clusters + 1] int64 DEVICE array; cluster c is the rows
+ *                 offsets[c] .. offsets[c+1]-1; offsets[0] == 0, nondecreasing
+ *   eps           [n_clusters] FP32 DEVICE array of per-cluster softening
+ *   n_total       offsets[n_clusters] (the total particle count)
+ * Asynchronous. Offsets and eps are not read back to the host: the caller
+ * guarantees they are valid (eps > 0, finite).
+ */
+nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const int64_t *offsets,
+                           int64_t n_clusters, int64_t n_total, const float *eps,
+                           float *a, float *p, nb_mode mode, void *stream);
+
+/*
+ * nsteps kick-drift-kick leap-frog steps, Eqs. (1)-(3) of Section "Method",
+ * with FP64 state on the device:
+ *   v += 1/2 g dt;  x += v dt;  g = -a(x) (Eq. (gravity), FP32 pair kernel);
+ *   v += 1/2 g dt
+ *   x    [n][3] FP64 device, in/out positions
+ *   v    [n][3] FP64 device, in/out velocities
+ *   m    [n]    FP32 device masses
+ *   a    [n][3] FP32 device: on entry Eq. (gravity) at the entry positions
+ *                (literal sign) if a_valid != 0, else it is computed first;
+ *                on exit Eq. (gravity) at the exit positions
+ *   p    [n]    FP32 device, out: potentials at the exit positions (may be NULL)
+ * Asynchronous. In NB_COMPENSATED mode the FP64 positions enter the pair
+ * kernel as FP32 offsets from per-tile reference points.
+ */
+nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
+                           int64_t n, float eps, double dt, int nsteps, int a_valid,
+                           nb_mode mode, void *stream);
+
+/*
+ * Total energy of an FP64 state: out_kw[0] = K = 1/2 sum m |v|^2 and
+ * out_kw[1] = W = -1/2 sum m_i p_i, accumulated in FP64 in a fixed order.
+ * x, v FP64 device [n][3]; m FP32 device [n]; out_kw HOST double[2].
+ * Synchronous (waits for `stream`).
+ */
+nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *m, int64_t n,
+                    float eps, double *out_kw, nb_mode mode, void *stream);
+
+/*
+ * Vector-Jacobian product of Eq. (gravity): for upstream gradients ga [n][3]
+ * on a and gp [n] on p, the gradient of L = sum_i ga_i . a_i + gp_i p_i with
+ * respect to the positions, gx [n][3], and masses, gm [n]. All FP32 device
+ * arrays. Computed as one gather pass over all pairs (no atomics), so the
+ * result is reproducible. Asynchronous.
+ */
+nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
+                       const float *ga, const float *gp, float *gx, float *gm, void *stream);
+
+/* Wait for `stream` and report device-side errors recorded by this context's
+ * kernels since the last check (NB_ERR_TIMEOUT if a bounded wait ran out). */
+nb_status nb_synchronize(nb_ctx *ctx, void *stream);
+
+/* Tile shape used for nb_force at size n in `mode` (the override if one is
+ * set, else the tuned entry for n's size class, else the built-in default). */
+nb_status nb_get_tile(nb_ctx *ctx, int64_t n, nb_mode mode, nb_tile *out);
+
+/* Force a tile shape for `mode` (must be one of the compiled shapes listed by
+ * nb_list_tiles); NULL clears the override. */
+nb_status nb_set_tile(nb_ctx *ctx, nb_mode mode, const nb_tile *tile);
+
+/* The compiled tile shapes of `mode`. Writes up to `cap` entries to out (may
+ * be NULL) and the total count to *count. */
+nb_status nb_list_tiles(nb_mode mode, nb_tile *out, int cap, int *count);
+
+/*
+ * Time every compiled tile shape on synthetic data of size n (the inputs are
+ * generated on the device by the library and only timing is kept), keep the
+ * fastest for n's size class and return it in *best with its rate in
+ * interactions per second in *rate (either may be NULL). Synchronous.
+ */
+nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_tile *best,
+                      double *rate);
+
+/* Per-kernel timing. With timing on, every kernel launch of this context is
+ * bracketed by CUDA events on its stream. nb_timing_read waits for those
+ * events and reports, for kernel class `kernel` (0 = pack, 1 = pair,
+ * 2 = reduce, 3 = leap-frog update, 4 = batched pair, 5 = vjp pair), the
+ * summed duration in ms and the launch count since the last reset. */
+nb_status nb_timing_enable(nb_ctx *ctx, int on);
+nb_status nb_timing_read(nb_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+nb_status nb_timing_reset(nb_ctx *ctx);
+
+/* Test hook for the bounded-wait path: with unit >= 0 the pair kernel's
+ * producer does not issue the copy of work unit `unit`, so the consumers'
+ * bounded wait runs out, the kernel records a timeout and returns, and the
+ * next nb_synchronize reports NB_ERR_TIMEOUT. wait_ns sets the wait limit
+ * (0 keeps the default of one second). -1 disables. */
+nb_status nb_debug_set_fault(nb_ctx *ctx, int64_t unit, int64_t wait_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

@@ -1,0 +1,65 @@
+// nb_ext.h -- services of the context (nb_capi.cu) used by the translation
+// units that implement the other entry points (leap-frog, batched, VJP).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "nb_internal.h"
+
+namespace nbx {
+
+// Grow-only device buffers owned by the context for the other entry points.
+struct ExtState {
+    static constexpr int kSlots = 12;
+    void *buf[kSlots] = {};
+    size_t cap[kSlots] = {};
+};
+void ext_release(ExtState &s);
+
+// Brackets one kernel launch with CUDA events on its stream when the
+// context's timing is on (nb_timing_enable).
+class TimedLaunch {
+  public:
+    TimedLaunch(nb_ctx *ctx, int kernel, cudaStream_t st);
+    ~TimedLaunch();
+    TimedLaunch(const TimedLaunch &) = delete;
+    TimedLaunch &operator=(const TimedLaunch &) = delete;
+
+  private:
+    nb_ctx *ctx_;
+    int kernel_;
+    cudaStream_t st_;
+    cudaEvent_t start_ = nullptr, stop_ = nullptr;
+};
+
+nb_status fail(nb_ctx *ctx, nb_status st, const std::string &m);
+nb_status cuda_fail(nb_ctx *ctx, cudaError_t e, const char *what);
+nb_status check_common(nb_ctx *ctx, int64_t n, float eps, int mode);
+
+int ctx_device(const nb_ctx *ctx);
+int ctx_sm_count(const nb_ctx *ctx);
+int *ctx_err_word(nb_ctx *ctx);
+uint64_t ctx_wait_ns(const nb_ctx *ctx);
+ExtState &ctx_ext(nb_ctx *ctx);
+
+cudaError_t ensure_buffer(void **ptr, size_t *cap, size_t bytes);
+int resident_ctas(nb_ctx *ctx, const nbk::PairVariant &v);
+const nbk::PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp);
+
+// pack (unless prepacked) -> pair -> combine, enqueued on st.
+nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const nbk::JPart *prepacked,
+                    int64_t n, float eps, float *a, float *p, bool comp, cudaStream_t st);
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace nbx

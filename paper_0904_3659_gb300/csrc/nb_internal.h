@@ -1,0 +1,86 @@
+// nb_internal.h -- host-side interface between the C ABI (nb_capi.cu) and the
+// kernel translation units. Not installed; not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/nbody.h"
+
+namespace nbk {
+
+// One particle as staged in shared memory for the pair kernel: 32 bytes,
+// every value duplicated so that one 64-bit register pair feeds both lanes
+// of a packed FP32x2 instruction. Positions are stored negated and the mass
+// as -m/2 (both exact): d = x_i + (-x_j) and the Newton step folds the
+// factor -1/2 into the mass (see nb_pair.cu).
+struct alignas(32) JPart {
+    float2 nx, ny, nz, hm;
+};
+static_assert(sizeof(JPart) == 32, "JPart must be 32 bytes");
+
+// Particle arrays are padded to a multiple of this (>= every i-block and
+// j-tile size) with inert entries (m = 0 at the origin).
+constexpr int64_t kPad = 1024;
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Arguments of the persistent pair kernel (one launch evaluates Eq. (gravity)
+// for all i of one system). Work unit u = (i-block u / njt, j-tile u % njt);
+// CTA c owns the contiguous units [c*units/grid, (c+1)*units/grid).
+struct PairArgs {
+    const JPart *jp;       // [npad] packed particles (source of both i and j)
+    float4 *partial;       // [grid][maxseg][words][ib] per-segment partial sums
+    int *err;              // device error word (bit kErrTimeout)
+    int64_t njt;           // j-tiles covering n
+    int64_t units;         // nib * njt
+    int grid;              // CTAs launched
+    int maxseg;            // max i-blocks one CTA touches
+    float eps2;            // eps^2 in FP32
+    int64_t fault_unit;    // test hook: unit whose copy is never issued (-1: none)
+    uint64_t wait_ns;      // limit of one bounded barrier wait
+};
+
+// Arguments of the deterministic cross-CTA combine.
+struct ReduceArgs {
+    const float4 *partial;
+    float *a;              // [n][3]
+    float *p;              // [n]
+    int64_t n;
+    int64_t njt;
+    int64_t units;
+    int grid;
+    int maxseg;
+    int ib;
+};
+
+// A compiled pair-kernel shape.
+struct PairVariant {
+    nb_tile tile;
+    bool comp;                 // Kahan-compensated accumulation
+    const void *kernel;        // for occupancy queries
+    size_t smem;               // dynamic shared memory bytes
+    cudaError_t (*launch)(const PairArgs &, int grid, size_t smem, cudaStream_t);
+};
+
+// Registry of compiled variants (nb_pair.cu).
+int pair_variant_count(bool comp);
+const PairVariant *pair_variant(bool comp, int idx);
+const PairVariant *pair_variant_find(bool comp, const nb_tile &t);
+int pair_default_index(bool comp, int64_t n);
+
+// Launchers (nb_pair.cu).
+cudaError_t launch_pack_f32(const float *x, const float *m, int64_t n, int64_t npad, JPart *jp,
+                            cudaStream_t st);
+cudaError_t launch_reduce(const ReduceArgs &r, bool comp, cudaStream_t st);
+cudaError_t launch_fill_uniform(float *x, float *m, int64_t n, uint64_t seed, cudaStream_t st);
+
+// Work decomposition of one nb_force call for a given variant.
+struct PairPlan {
+    int64_t n, npad, nib, njt, units;
+    int grid, maxseg, ib, words;
+    size_t partial_bytes;
+};
+PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas);
+
+}  // namespace nbk

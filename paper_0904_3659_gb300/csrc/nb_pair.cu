@@ -1,0 +1,454 @@
+// nb_pair.cu -- the pair kernel of Eq. (gravity) (Fujiwara & Nakasato,
+// arXiv:0904.3659, Section "Introduction") for sm_103a, with its pack and
+// combine kernels.
+//
+// Design (GB300-first; the paper's RV770 unrolled loops, Figs. 1-3, are prior
+// art whose idea -- reuse one loaded x_j for several i -- is kept):
+//  * Each thread holds IPT i-particles in registers, as IPT/2 packed pairs,
+//    and every interaction is evaluated with packed FP32x2 instructions
+//    (two i against the same j per instruction), which halves the issue
+//    slots the FP32 work takes and leaves room for the special-function
+//    unit's reciprocal square root and the shared-memory loads.
+//  * j-particles stream through shared memory in tiles of JT, copied by the
+//    tensor memory accelerator (1-D bulk copies) into STAGES buffers with
+//    mbarrier completion; every wait is bounded.
+//  * The kernel is persistent: the grid is the number of CTAs that fit on the
+//    GPU at once, and the (i-block, j-tile) work units are split into equal
+//    contiguous ranges, one per CTA, so every SM gets the same work however
+//    N divides. A CTA that covers only part of an i-block's j range writes a
+//    partial sum; a second kernel adds the partials of each i-block in CTA
+//    order. No float atomics: results are bit-reproducible for a fixed launch.
+//  * Per interaction: 16 FP32 lane operations + 1 reciprocal square root:
+//      d  = x_i - x_j                      3 add
+//      s  = eps^2 + d.d                    3 fma
+//      y  = rsqrt(s)                       1 special-function op
+//      Newton step folded into the mass:   y2 = y*y, t = s*y2 - 3, u = y*t
+//        (the refined value is y1 = -u/2, see tile_pass)
+//      q  = (-m_j/2) * u = m_j y1          1 mul     p_i += q   1 add
+//      w  = q * u*u     = 4 m_j y1^3       2 mul
+//      a_i += w d                           3 fma
+//    a_i carries a factor 4 that the combine removes (an exact scaling).
+#include <algorithm>
+#include <cstdio>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+
+namespace nbk {
+using namespace nbdev;
+
+// ---------------------------------------------------------------------------
+// Pack: x [n][3], m [n] -> JPart [npad]; rows n..npad-1 are inert (m = 0 at 0).
+__global__ void pack_f32_kernel(const float *__restrict__ x, const float *__restrict__ m,
+                                int64_t n, int64_t npad, JPart *__restrict__ jp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < n) {
+        const float px = x[3 * i + 0], py = x[3 * i + 1], pz = x[3 * i + 2];
+        const float hm = -0.5f * m[i];
+        lo = make_float4(-px, -px, -py, -py);
+        hi = make_float4(-pz, -pz, hm, hm);
+    }
+    float4 *dst = reinterpret_cast<float4 *>(jp + i);
+    dst[0] = lo;
+    dst[1] = hi;
+}
+
+// ---------------------------------------------------------------------------
+// One pass of a j-tile against the thread's P pairs of i-particles.
+// acc[q][0..2] += 4 m_j y1^3 (x_i - x_j), acc[q][3] += m_j y1, where
+// y1 = y (3 - s y^2) / 2 is one Newton-Raphson step for f(y) = y^-2 - s from
+// the special-function unit's estimate y of s^{-1/2}. With t = s y^2 - 3 and
+// u = y t we have y1 = -u/2, so m_j y1 = (-m_j/2) u (the packed mass is
+// stored as -m_j/2) and 4 m_j y1^3 = (m_j y1) u^2.
+// In a diagonal tile (DIAG) the j == i term is removed by zeroing the mass
+// lane of the thread's own particle; self0/self1 give, per pair, the tile
+// position of the thread's own i (outside [0, JT) when it is not here).
+template <int P, int JT, int UNR, bool DIAG>
+__device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const float2 (&xi)[P],
+                                          const float2 (&yi)[P], const float2 (&zi)[P],
+                                          float2 (&acc)[P][4], const float2 eps2,
+                                          const int (&self0)[P], const int (&self1)[P]) {
+    const float2 m3 = splat2(-3.f);
+#pragma unroll UNR
+    for (int jj = 0; jj < JT; ++jj) {
+        const float4 A = reinterpret_cast<const float4 *>(T + jj)[0];
+        const float4 B = reinterpret_cast<const float4 *>(T + jj)[1];
+        const float2 nxj = make_float2(A.x, A.y);
+        const float2 nyj = make_float2(A.z, A.w);
+        const float2 nzj = make_float2(B.x, B.y);
+        const float2 hmj = make_float2(B.z, B.w);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float2 dx = add2(xi[q], nxj);
+            const float2 dy = add2(yi[q], nyj);
+            const float2 dz = add2(zi[q], nzj);
+            float2 s = fma2(dx, dx, eps2);
+            s = fma2(dy, dy, s);
+            s = fma2(dz, dz, s);
+            const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
+            const float2 y2 = mul2(y, y);
+            const float2 t = fma2(s, y2, m3);
+            const float2 u = mul2(y, t);
+            float2 hm = hmj;
+            if (DIAG) {
+                if (jj == self0[q]) hm.x = 0.f;
+                if (jj == self1[q]) hm.y = 0.f;
+            }
+            const float2 qv = mul2(hm, u);
+            acc[q][3] = add2(acc[q][3], qv);
+            const float2 u2 = mul2(u, u);
+            const float2 w = mul2(qv, u2);
+            acc[q][0] = fma2(w, dx, acc[q][0]);
+            acc[q][1] = fma2(w, dy, acc[q][1]);
+            acc[q][2] = fma2(w, dz, acc[q][2]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent pair kernel. See PairArgs for the work split.
+template <int THREADS, int IPT, int JT, int STAGES, bool COMP>
+__global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
+    static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
+    constexpr int P = IPT / 2;
+    constexpr int IB = THREADS * IPT;
+    constexpr uint32_t TILE_BYTES = JT * sizeof(JPart);
+    constexpr int UNR = 4;
+    static_assert(TILE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+    // i-blocks and j-tiles must tile the padded particle array exactly, so
+    // that every i and j the kernel touches lies inside it.
+    static_assert(kPad % IB == 0 && kPad % JT == 0, "tile sizes must divide the padding");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    JPart *tiles = reinterpret_cast<JPart *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES);
+
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    const int64_t u0 = c * args.units / args.grid;
+    const int64_t u1 = (c + 1) * args.units / args.grid;
+    const int64_t count = u1 - u0;
+    const int64_t bfirst = u0 / args.njt;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // Producer state (thread 0): units u0 .. u0+issued-1 have been issued.
+    int64_t issued = 0;
+    auto issue_next = [&]() {
+        const int64_t u = u0 + issued;
+        const int s = (int)(issued % STAGES);
+        if (u != args.fault_unit) {
+            const int64_t jt = u % args.njt;
+            mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+            bulk_g2s(tiles + (size_t)s * JT, args.jp + jt * JT, TILE_BYTES, &full[s]);
+        }
+        ++issued;
+    };
+    if (tid == 0)
+        while (issued < count && issued < STAGES - 1) issue_next();
+
+    float2 xi[P], yi[P], zi[P];
+    float2 sum[P][4], cmp[P][4];
+    const float2 eps2 = splat2(args.eps2);
+    const float2 zero2 = splat2(0.f);
+
+    auto flush = [&](int64_t b) {
+        const int64_t seg = b - bfirst;
+        float4 *dst = args.partial + (c * args.maxseg + seg) * (COMP ? 2 : 1) * (int64_t)IB;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int i0 = (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+            dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
+            dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+            if (COMP) {
+                dst[IB + i0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
+                dst[IB + i1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
+            }
+        }
+    };
+
+    int64_t cur_b = -1;
+    int bad = 0;
+    int64_t k = 0;
+    for (; k < count; ++k) {
+        // Every thread is done with iteration k-1, so its stage may be
+        // refilled; a timeout seen by any thread ends the loop for all.
+        if (__syncthreads_or(bad)) break;
+        if (tid == 0 && issued < count) issue_next();
+
+        const int64_t u = u0 + k;
+        const int64_t b = u / args.njt;
+        const int64_t jt = u - b * args.njt;
+        if (b != cur_b) {
+            if (cur_b >= 0) flush(cur_b);
+            cur_b = b;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int64_t i0 = b * IB + (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+                const float4 A0 = reinterpret_cast<const float4 *>(args.jp + i0)[0];
+                const float4 B0 = reinterpret_cast<const float4 *>(args.jp + i0)[1];
+                const float4 A1 = reinterpret_cast<const float4 *>(args.jp + i1)[0];
+                const float4 B1 = reinterpret_cast<const float4 *>(args.jp + i1)[1];
+                xi[q] = make_float2(-A0.x, -A1.x);
+                yi[q] = make_float2(-A0.z, -A1.z);
+                zi[q] = make_float2(-B0.x, -B1.x);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    sum[q][r] = zero2;
+                    cmp[q][r] = zero2;
+                }
+            }
+        }
+
+        const int s = (int)(k % STAGES);
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((k / STAGES) & 1), args.wait_ns)) {
+            bad = 1;
+            continue;
+        }
+        const JPart *T = tiles + (size_t)s * JT;
+
+        float2 acc[P][4];
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
+
+        const int64_t ibase = b * IB, jbase = jt * JT;
+        int self0[P], self1[P];
+        if (jbase < ibase + IB && ibase < jbase + JT) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
+                self1[q] = self0[q] + THREADS;
+            }
+            tile_pass<P, JT, 1, true>(T, xi, yi, zi, acc, eps2, self0, self1);
+        } else {
+            tile_pass<P, JT, UNR, false>(T, xi, yi, zi, acc, eps2, self0, self1);
+        }
+
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (COMP) {
+                    // Kahan: the running sum's lost low part is kept in cmp
+                    // (true value = sum - cmp).
+                    const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
+                    const float2 t = add2(sum[q][r], y);
+                    cmp[q][r] = add2(add2(t, neg2(sum[q][r])), neg2(y));
+                    sum[q][r] = t;
+                } else {
+                    sum[q][r] = add2(sum[q][r], acc[q][r]);
+                }
+            }
+    }
+
+    bad = __syncthreads_or(bad);
+    if (!bad) {
+        if (cur_b >= 0) flush(cur_b);
+        return;
+    }
+    if (tid == 0) {
+        atomicOr(args.err, kErrTimeout);
+        // Let every copy still in flight land before this CTA's shared
+        // memory is released. The unit that failed is k-1 (or the last one).
+        for (int64_t kk = (k > 0 ? k - 1 : 0); kk < issued; ++kk) {
+            if (u0 + kk == args.fault_unit) continue;
+            mbar_wait_bounded(&full[kk % STAGES], (uint32_t)((kk / STAGES) & 1), args.wait_ns);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Combine: for each i, add the partials of its i-block in CTA order and
+// remove the factor 4 carried by the acceleration sums.
+__device__ __forceinline__ int64_t cta_of_unit(int64_t u, int64_t units, int grid) {
+    return ((u + 1) * (int64_t)grid - 1) / units;
+}
+
+__global__ void reduce_plain_kernel(const ReduceArgs r) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    const int64_t b = i / r.ib, w = i - b * r.ib;
+    const int64_t clo = cta_of_unit(b * r.njt, r.units, r.grid);
+    const int64_t chi = cta_of_unit(b * r.njt + r.njt - 1, r.units, r.grid);
+    float ax = 0.f, ay = 0.f, az = 0.f, pp = 0.f;
+    for (int64_t c = clo; c <= chi; ++c) {
+        const int64_t bf = (c * r.units / r.grid) / r.njt;
+        const float4 v = r.partial[(c * r.maxseg + (b - bf)) * r.ib + w];
+        ax = __fadd_rn(ax, v.x);
+        ay = __fadd_rn(ay, v.y);
+        az = __fadd_rn(az, v.z);
+        pp = __fadd_rn(pp, v.w);
+    }
+    r.a[3 * i + 0] = 0.25f * ax;
+    r.a[3 * i + 1] = 0.25f * ay;
+    r.a[3 * i + 2] = 0.25f * az;
+    r.p[i] = pp;
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+__global__ void reduce_comp_kernel(const ReduceArgs r) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    const int64_t b = i / r.ib, w = i - b * r.ib;
+    const int64_t clo = cta_of_unit(b * r.njt, r.units, r.grid);
+    const int64_t chi = cta_of_unit(b * r.njt + r.njt - 1, r.units, r.grid);
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t c = clo; c <= chi; ++c) {
+        const int64_t bf = (c * r.units / r.grid) / r.njt;
+        const int64_t base = (c * r.maxseg + (b - bf)) * 2 * r.ib + w;
+        const float4 hi = r.partial[base];
+        const float4 lo = r.partial[base + r.ib];
+        const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+        const float l[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float s, e;
+            two_sum(S[q], h[q], s, e);
+            S[q] = s;
+            E[q] = __fadd_rn(E[q], __fsub_rn(e, l[q]));  // segment value = hi - lo
+        }
+    }
+    r.a[3 * i + 0] = 0.25f * __fadd_rn(S[0], E[0]);
+    r.a[3 * i + 1] = 0.25f * __fadd_rn(S[1], E[1]);
+    r.a[3 * i + 2] = 0.25f * __fadd_rn(S[2], E[2]);
+    r.p[i] = __fadd_rn(S[3], E[3]);
+}
+
+// Synthetic inputs for tuning runs (timing only; values do not matter
+// beyond being finite): x uniform in [-1, 1)^3 from a 64-bit mixer, m = 1/n.
+__global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 3; ++c) {
+        uint64_t z = seed + (uint64_t)(3 * i + c) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[3 * i + c] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    }
+    m[i] = 1.0f / (float)n;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers and the registry of compiled shapes.
+template <int T, int I, int J, int S, bool C>
+static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
+    pair_kernel<T, I, J, S, C><<<grid, T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S, int J>
+constexpr size_t pair_smem() {
+    return (size_t)S * J * sizeof(JPart) + (size_t)S * sizeof(uint64_t);
+}
+
+#define NB_VARIANT(T, I, J, S, C) \
+    {{T, I, J, S}, C, (const void *)pair_kernel<T, I, J, S, C>, pair_smem<S, J>(), launch_pair<T, I, J, S, C>}
+
+// Plain shapes: the first entries are the defaults for small and large n.
+static const PairVariant kPlain[] = {
+    NB_VARIANT(128, 4, 256, 3, false),  // 0: large-n default
+    NB_VARIANT(64, 2, 64, 4, false),    // 1: small-n default
+    NB_VARIANT(128, 8, 256, 3, false),
+    NB_VARIANT(256, 4, 256, 3, false),
+    NB_VARIANT(128, 4, 512, 2, false),
+    NB_VARIANT(128, 2, 128, 4, false),
+    NB_VARIANT(256, 2, 128, 4, false),
+    NB_VARIANT(64, 4, 128, 4, false),
+};
+static const PairVariant kComp[] = {
+    NB_VARIANT(128, 4, 256, 3, true),   // 0: large-n default
+    NB_VARIANT(64, 2, 64, 4, true),     // 1: small-n default
+    NB_VARIANT(128, 2, 128, 4, true),
+    NB_VARIANT(256, 4, 256, 3, true),
+    NB_VARIANT(128, 4, 512, 2, true),
+    NB_VARIANT(256, 2, 128, 4, true),
+};
+#undef NB_VARIANT
+
+int pair_variant_count(bool comp) {
+    return comp ? (int)(sizeof(kComp) / sizeof(kComp[0])) : (int)(sizeof(kPlain) / sizeof(kPlain[0]));
+}
+
+const PairVariant *pair_variant(bool comp, int idx) {
+    if (idx < 0 || idx >= pair_variant_count(comp)) return nullptr;
+    return comp ? &kComp[idx] : &kPlain[idx];
+}
+
+const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
+    for (int k = 0; k < pair_variant_count(comp); ++k) {
+        const nb_tile &v = pair_variant(comp, k)->tile;
+        if (v.threads == t.threads && v.ipt == t.ipt && v.jtile == t.jtile && v.stages == t.stages)
+            return pair_variant(comp, k);
+    }
+    return nullptr;
+}
+
+int pair_default_index(bool comp, int64_t n) {
+    (void)comp;
+    return n >= (int64_t)1 << 16 ? 0 : 1;
+}
+
+PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
+    PairPlan p{};
+    p.n = n;
+    p.ib = v.tile.threads * v.tile.ipt;
+    p.npad = round_up(std::max<int64_t>(n, 1), kPad);
+    p.nib = (n + p.ib - 1) / p.ib;
+    p.njt = (n + v.tile.jtile - 1) / v.tile.jtile;
+    p.units = p.nib * p.njt;
+    p.grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.units, resident_ctas));
+    int maxseg = 1;
+    for (int64_t c = 0; c < p.grid; ++c) {
+        const int64_t u0 = c * p.units / p.grid, u1 = (c + 1) * p.units / p.grid;
+        if (u1 <= u0) continue;
+        maxseg = std::max<int>(maxseg, (int)((u1 - 1) / p.njt - u0 / p.njt + 1));
+    }
+    p.maxseg = maxseg;
+    p.words = v.comp ? 2 : 1;
+    p.partial_bytes = (size_t)p.grid * p.maxseg * p.words * p.ib * sizeof(float4);
+    return p;
+}
+
+cudaError_t launch_pack_f32(const float *x, const float *m, int64_t n, int64_t npad, JPart *jp,
+                            cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = (npad + threads - 1) / threads;
+    pack_f32_kernel<<<(unsigned)blocks, threads, 0, st>>>(x, m, n, npad, jp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ReduceArgs &r, bool comp, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = (r.n + threads - 1) / threads;
+    if (comp)
+        reduce_comp_kernel<<<(unsigned)blocks, threads, 0, st>>>(r);
+    else
+        reduce_plain_kernel<<<(unsigned)blocks, threads, 0, st>>>(r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_uniform(float *x, float *m, int64_t n, uint64_t seed, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = (n + threads - 1) / threads;
+    fill_uniform_kernel<<<(unsigned)blocks, threads, 0, st>>>(x, m, n, seed);
+    return cudaGetLastError();
+}
+
+}  // namespace nbk

@@ -1,0 +1,59 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, and
+exports every entry point include/nbody.h declares. No compute calls."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nbody.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nb_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0904_3659_gb300 import build
+    build.build()
+    import paper_0904_3659_gb300 as nb
+    return nb
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("nb_create", "nb_destroy", "nb_last_error", "nb_force", "nb_force_batched",
+                     "nb_leapfrog_step", "nb_force_vjp", "nb_energy", "nb_synchronize",
+                     "nb_autotune"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(lib.library_path)
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+    # The binding wraps exactly the declared set, under the same names.
+    assert sorted(lib.exported_symbols) == declared_functions()
+
+
+def test_host_only_calls(lib):
+    assert lib.nb_status_string(lib.NB_ERR_TIMEOUT) == "NB_ERR_TIMEOUT"
+    tiles = lib.nb_list_tiles(lib.NB_PLAIN)
+    assert len(tiles) >= 4
+    for t in tiles + lib.nb_list_tiles(lib.NB_COMPENSATED):
+        ib = t.threads * t.ipt
+        assert t.ipt % 2 == 0 and 1024 % ib == 0 and 1024 % t.jtile == 0 and t.stages >= 2
+        assert (t.jtile * 32) % 16 == 0
+
+
+def test_create_reports_error_without_gpu(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lib.NBError) as e:
+        lib.Context(0)
+    assert e.value.status in (lib.NB_ERR_CUDA, lib.NB_ERR_ARG)

@@ -1,0 +1,242 @@
+"""GPU parity of nb_force (Eq. (gravity)) against the FP64 oracle.
+
+Acceptance metric (per particle, max over particles):
+  e_a,i = |a_gpu,i - a_ref,i| / A_i,  A_i = sum_{j != i} m_j |x_i - x_j| / s_ij^{3/2}
+  e_p,i = |p_gpu,i - p_ref,i| / p_i
+A_i equals |a_i| when the terms do not cancel and keeps the measure
+well-posed near the centre of a cluster, where a_i -> 0 by symmetry.
+Tolerances: 1e-5 (NB_PLAIN), 1e-6 (NB_COMPENSATED).
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def nb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0904_3659_gb300 import build
+    build.build()
+    import paper_0904_3659_gb300 as nbmod
+    return nbmod
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    c = nb.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_force(nb, ctx, x32, m32, eps, mode):
+    import torch
+    n = x32.shape[0]
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(np.ascontiguousarray(x32)).to(dev)
+    mt = torch.from_numpy(np.ascontiguousarray(m32)).to(dev)
+    a = torch.full((n, 3), float("nan"), dtype=torch.float32, device=dev)
+    p = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+    nb.nb_force(ctx, xt, mt, n, eps, a, p, mode)
+    nb.nb_synchronize(ctx)
+    return a.cpu().numpy(), p.cpu().numpy()
+
+
+def rel_errors(a, p, ra, rp, ramag):
+    da = np.linalg.norm(a.astype(np.float64) - ra, axis=1)
+    dp = np.abs(p.astype(np.float64) - rp)
+    ea = np.where(ramag > 0, da / np.where(ramag > 0, ramag, 1.0), da)
+    ep = np.where(rp > 0, dp / np.where(rp > 0, rp, 1.0), dp)
+    return ea, ep
+
+
+def plummer32(n, seed=0):
+    x, _, m = workloads.plummer(n, seed=seed)
+    return x.astype(np.float32), m.astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 127, 1000, 1023, 1025, 4097, 6000])
+def test_ragged_sizes(nb, ctx, oracle_mod, n, mode):
+    x32, m32 = plummer32(n, seed=n)
+    eps = np.float32(0.01)
+    a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    ea, ep = rel_errors(a, p, ra, rp, ramag)
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(p))
+    assert ea.max() <= TOL[mode], ea.max()
+    assert ep.max() <= TOL[mode], ep.max()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plummer4096_full(nb, ctx, oracle_mod, mode):
+    # Single force + potential evaluation, N = 4096 equal-mass Plummer sphere,
+    # eps = 0.01, one call to nb_force, full oracle.
+    w = workloads.WORKLOADS["plummer4096"]
+    x32, m32 = plummer32(w["n"], w["seed"])
+    eps = np.float32(w["eps"])
+    a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    ea, ep = rel_errors(a, p, ra, rp, ramag)
+    assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode], (ea.max(), ep.max())
+    # Momentum invariant sum_i m_i a_i = 0, to FP32 accuracy of the sums.
+    mom = np.abs((m32[:, None].astype(np.float64) * a).sum(0)).max()
+    assert mom <= 1e-5 * (m32 * ramag).sum()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_every_tile_shape(nb, ctx, oracle_mod, mode):
+    # Each compiled tile shape at a size that spans several i-blocks and
+    # j-tiles with a ragged tail.
+    n = 3001
+    x32, m32 = plummer32(n, seed=7)
+    eps = np.float32(1.0 / 64)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    try:
+        for tile in nb.nb_list_tiles(mode):
+            nb.nb_set_tile(ctx, mode, tile)
+            a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+            ea, ep = rel_errors(a, p, ra, rp, ramag)
+            assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode], (tile, ea.max(), ep.max())
+    finally:
+        nb.nb_set_tile(ctx, mode, None)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_bitwise_repeatable(nb, ctx, mode):
+    x32, m32 = plummer32(20000, seed=3)
+    a1, p1 = gpu_force(nb, ctx, x32, m32, np.float32(0.01), mode)
+    a2, p2 = gpu_force(nb, ctx, x32, m32, np.float32(0.01), mode)
+    assert a1.tobytes() == a2.tobytes() and p1.tobytes() == p2.tobytes()
+
+
+def test_coincident_and_self(nb, ctx, oracle_mod):
+    # Duplicated positions: distinct coincident particles are summed, the
+    # self term is not.
+    rng = np.random.default_rng(5)
+    base = rng.normal(size=(700, 3)).astype(np.float32)
+    x32 = np.concatenate([base, base[:300]])
+    m32 = rng.uniform(0.5, 1.5, 1000).astype(np.float32)
+    eps = np.float32(0.05)
+    for mode in (0, 1):
+        a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+        ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+        ea, ep = rel_errors(a, p, ra, rp, ramag)
+        assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode]
+
+
+def test_power_of_two_scaling_exact(nb, ctx):
+    # x -> 2x, eps -> 2eps scales every FP32 operation of the kernel by a
+    # power of two: the outputs must be exactly a/4, p/2.
+    x32, m32 = plummer32(5000, seed=9)
+    for mode in (0, 1):
+        a1, p1 = gpu_force(nb, ctx, x32, m32, np.float32(0.125), mode)
+        a2, p2 = gpu_force(nb, ctx, 2 * x32, m32, np.float32(0.25), mode)
+        np.testing.assert_array_equal(a2, a1 / 4)
+        np.testing.assert_array_equal(p2, p1 / 2)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plummer65536_full(nb, ctx, oracle_mod, mode):
+    w = workloads.WORKLOADS["plummer65536_kdk16"]
+    x32, m32 = plummer32(w["n"], w["seed"])
+    eps = np.float32(w["eps"])
+    a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    ea, ep = rel_errors(a, p, ra, rp, ramag)
+    assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode], (ea.max(), ep.max())
+
+
+@pytest.fixture(scope="module")
+def plummer1m(oracle_mod):
+    w = workloads.WORKLOADS["plummer1m"]
+    x32, m32 = plummer32(w["n"], w["seed"])
+    rows = workloads.sample_rows(w["n"], w["sample"], w["sample_seed"])
+    eps = np.float32(w["eps"])
+    ra, rp, ramag = oracle_mod.force_rows(x32, m32, eps, rows)
+    return x32, m32, eps, rows, ra, rp, ramag
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plummer1m_sampled_every_tile(nb, ctx, plummer1m, mode):
+    # N = 2^20, eps = 1/256: every compiled shape (the benchmark runs one of
+    # them), checked on 2048 sampled rows against the FP64 oracle.
+    x32, m32, eps, rows, ra, rp, ramag = plummer1m
+    try:
+        for tile in nb.nb_list_tiles(mode):
+            nb.nb_set_tile(ctx, mode, tile)
+            a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+            ea, ep = rel_errors(a[rows], p[rows], ra, rp, ramag)
+            assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode], (tile, ea.max(), ep.max())
+    finally:
+        nb.nb_set_tile(ctx, mode, None)
+
+
+def test_argument_errors(nb, ctx):
+    import torch
+    dev = torch.device("cuda:0")
+    x = torch.zeros((4, 3), device=dev)
+    m = torch.ones(4, device=dev)
+    a = torch.empty((4, 3), device=dev)
+    p = torch.empty(4, device=dev)
+    for eps in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(nb.NBError) as e:
+            nb.nb_force(ctx, x, m, 4, eps, a, p)
+        assert e.value.status == nb.NB_ERR_ARG
+    with pytest.raises(nb.NBError) as e:
+        nb.nb_force(ctx, x, m, -1, 0.1, a, p)
+    assert e.value.status == nb.NB_ERR_ARG
+    with pytest.raises(nb.NBError) as e:
+        nb.nb_force(ctx, None, m, 4, 0.1, a, p)
+    assert e.value.status == nb.NB_ERR_ARG
+    with pytest.raises(nb.NBError) as e:
+        nb.nb_force(ctx, x, m, 4, 0.1, a, p, mode=7)
+    assert e.value.status == nb.NB_ERR_ARG
+    # n == 0 is a valid no-op, even with NULL pointers.
+    nb.nb_force(ctx, None, None, 0, 0.1, None, None)
+    with pytest.raises(nb.NBError) as e:
+        nb.nb_set_tile(ctx, 0, (96, 3, 100, 2))
+    assert e.value.status == nb.NB_ERR_ARG
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(nb, ctx, oracle_mod):
+    # The producer skips the copy of one work unit, so the consumers' bounded
+    # wait (0.2 s here) runs out; the kernel records a timeout and returns,
+    # and nb_synchronize reports it. Nothing hangs or faults, and the next
+    # call on the same context is correct.
+    x32, m32 = plummer32(4096, seed=0)
+    eps = np.float32(0.01)
+    nb.nb_debug_set_fault(ctx, 3, 200_000_000)
+    try:
+        import torch
+        dev = torch.device("cuda:0")
+        xt = torch.from_numpy(x32).to(dev)
+        mt = torch.from_numpy(m32).to(dev)
+        a = torch.empty((4096, 3), device=dev)
+        p = torch.empty(4096, device=dev)
+        nb.nb_force(ctx, xt, mt, 4096, eps, a, p)
+        with pytest.raises(nb.NBError) as e:
+            nb.nb_synchronize(ctx)
+        assert e.value.status == nb.NB_ERR_TIMEOUT
+    finally:
+        nb.nb_debug_set_fault(ctx, -1, 0)
+    a, p = gpu_force(nb, ctx, x32, m32, eps, 0)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    ea, ep = rel_errors(a, p, ra, rp, ramag)
+    assert ea.max() <= 1e-5 and ep.max() <= 1e-5
+
+
+def test_force_host_matches_device(nb, ctx):
+    x32, m32 = plummer32(5000, seed=12)
+    a_dev, p_dev = gpu_force(nb, ctx, x32, m32, np.float32(0.01), 0)
+    a = np.empty((5000, 3), np.float32)
+    p = np.empty(5000, np.float32)
+    nb.nb_force_host(ctx, x32.ctypes.data, m32.ctypes.data, 5000, np.float32(0.01),
+                     a.ctypes.data, p.ctypes.data, 0)
+    assert a.tobytes() == a_dev.tobytes() and p.tobytes() == p_dev.tobytes()
