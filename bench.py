@@ -214,7 +214,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
 
     w = workloads.WORKLOADS[WORKLOAD]
-    n, eps = w["n"], np.float32(w["eps"])
+    n, eps = (args.n or w["n"]), np.float32(w["eps"])
     x32, m32 = make_inputs(n, w["seed"])
     xt = torch.from_numpy(x32).to(dev)
     mt = torch.from_numpy(m32).to(dev)
@@ -226,9 +226,12 @@ def run_ours(args):
     # Tile choice: tune on a quarter-size proxy (same inner loop; the
     # persistent split balances the full size), then fix it.
     tiles = {}
-    for mode in (nb.NB_PLAIN, nb.NB_COMPENSATED):
-        if args.tile_tune:
-            t, _ = nb.nb_autotune(ctx, n // 4, mode)
+    for mode in ((nb.NB_PLAIN,) if args.plain_only else (nb.NB_PLAIN, nb.NB_COMPENSATED)):
+        fixed = args.tile if mode == nb.NB_PLAIN else args.tile_comp
+        if fixed:
+            nb.nb_set_tile(ctx, mode, tuple(int(v) for v in fixed.split(",")))
+        elif args.tile_tune:
+            t, _ = nb.nb_autotune(ctx, max(n // 4, 1024), mode)
             nb.nb_set_tile(ctx, mode, t)
         tiles[mode] = nb.nb_get_tile(ctx, n, mode)
         nb.nb_reserve(ctx, n, mode)
@@ -264,9 +267,13 @@ def run_ours(args):
         plain_ms, plain_k = timed(nb.NB_PLAIN, args.steps, args.warmup)
         a_plain = a.cpu().numpy()
         p_plain = p.cpu().numpy()
-        comp_ms, comp_k = timed(nb.NB_COMPENSATED, args.steps, args.warmup)
-        a_comp = a.cpu().numpy()
-        p_comp = p.cpu().numpy()
+        if args.plain_only:
+            comp_ms, comp_k = plain_ms, plain_k
+            a_comp, p_comp = a_plain, p_plain
+        else:
+            comp_ms, comp_k = timed(nb.NB_COMPENSATED, args.steps, args.warmup)
+            a_comp = a.cpu().numpy()
+            p_comp = p.cpu().numpy()
     clocks = clk.summary()
 
     ms_plain = max_over_ranks(sum(plain_ms) / len(plain_ms), world)
@@ -281,18 +288,18 @@ def run_ours(args):
     hm = torch.from_numpy(m32).pin_memory()
     ha = torch.empty((n, 3), dtype=torch.float32).pin_memory()
     hp = torch.empty((n,), dtype=torch.float32).pin_memory()
-    for _ in range(max(1, min(args.warmup, 2))):
+    for _ in range(max(1, min(args.warmup, 2)) if args.e2e else 0):
         nb.nb_force_host(ctx, hx.data_ptr(), hm.data_ptr(), n, eps, ha.data_ptr(), hp.data_ptr(),
                          nb.NB_PLAIN, stream)
     barrier(world)
     e2e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 3)) if args.e2e else 0):
         t0 = time.perf_counter()
         nb.nb_force_host(ctx, hx.data_ptr(), hm.data_ptr(), n, eps, ha.data_ptr(), hp.data_ptr(),
                          nb.NB_PLAIN, stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     barrier(world)
-    e2e_ms_max = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
+    e2e_ms_max = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world) if e2e_ms else float("nan")
 
     # Roofline of the dominant kernel (the pair kernel): FP32 pipe bound.
     peaks = measured_peaks()
@@ -324,14 +331,15 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic Plummer sphere (seed 0), float32",
-        "config": {"workload": WORKLOAD, "n": n, "eps": float(eps), "mode": "plain",
+        "config": {"workload": WORKLOAD if n == w["n"] else f"plummer n={n} (small case)",
+                   "n": n, "eps": float(eps), "mode": "plain",
                    "tile": list(tiles[nb.NB_PLAIN].as_tuple()),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "gflops_38": value * FLOP_PER_INT_PAPER / 1e9,
         "compensated": {"value": value_comp / 1e9, "unit": "G-int/s", "ms_per_step": ms_comp,
                         "slowdown_vs_plain": ms_comp / ms_plain,
-                        "tile": list(tiles[nb.NB_COMPENSATED].as_tuple()),
+                        "tile": list(tiles.get(nb.NB_COMPENSATED, tiles[nb.NB_PLAIN]).as_tuple()),
                         "pair_ms": comp_pair_ms},
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in plain_k.items()},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G-int/s",
@@ -341,9 +349,9 @@ def run_ours(args):
                                f"(+{MUFU_PER_INT} MUFU rsqrt, not binding); sm_max_mhz of "
                                f"{'measured' if peaks else 'nvidia-smi'} peaks"),
                      "frac_17op_convention": achieved / peak17},
-        "e2e": {"value": interactions * world / (e2e_ms_max * 1e-3) / 1e9, "unit": "G-int/s",
-                "h2d_bytes_per_step": int(x32.nbytes + m32.nbytes),
-                "d2h_bytes_per_step": int(4 * n * 3 + 4 * n)},
+        "e2e": ({"value": interactions * world / (e2e_ms_max * 1e-3) / 1e9, "unit": "G-int/s",
+                 "h2d_bytes_per_step": int(x32.nbytes + m32.nbytes),
+                 "d2h_bytes_per_step": int(4 * n * 3 + 4 * n)} if e2e_ms else None),
         "gpu_launches": 3 * args.steps * 2,
         "clocks": clocks,
     }
@@ -419,6 +427,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tile-tune", dest="tile_tune", action="store_false")
+    # Small-case options for profiler captures (the default run uses none).
+    ap.add_argument("--n", type=int, default=0, help="override N (profiling small cases)")
+    ap.add_argument("--tile", default="", help="plain tile: threads,ipt,jtile,stages")
+    ap.add_argument("--tile-comp", default="", help="compensated tile: threads,ipt,jtile,stages")
+    ap.add_argument("--plain-only", action="store_true")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":

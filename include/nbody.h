@@ -70,14 +70,24 @@ typedef enum nb_mode { NB_PLAIN = 0, NB_COMPENSATED = 1 } nb_mode;
 
 typedef struct nb_ctx nb_ctx;
 
-/* Tile shape of the pair kernel: `threads` per CTA, `ipt` i-particles per
- * thread held in registers (even: they are processed in packed FP32 pairs),
- * `jtile` j-particles per shared-memory stage, `stages` stages in flight. */
+/* Tile shape and schedule of the pair kernel: `threads` per CTA, `ipt`
+ * i-particles per thread held in registers (even: they are processed in
+ * packed FP32 pairs), `jtile` j-particles per shared-memory stage, `stages`
+ * stages in flight, `unroll` unroll factor of the j loop, `minblocks` the
+ * resident CTAs per SM the register allocation is held to, and `release`
+ * how a consumed stage is refilled (0: CTA barrier per tile; 1: the last
+ * warp to finish the tile issues the next copy, no barrier), `sums_in_smem`
+ * whether the running sums between tiles live in shared memory (1) or in
+ * registers (0). */
 typedef struct nb_tile {
     int threads;
     int ipt;
     int jtile;
     int stages;
+    int unroll;
+    int minblocks;
+    int release;
+    int sums_in_smem;
 } nb_tile;
 
 /* Create a context on CUDA device `device`. *out receives the handle. */

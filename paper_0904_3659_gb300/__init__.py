@@ -48,13 +48,15 @@ library_path = os.path.join(_HERE, "libnbody.so")
 
 class nb_tile(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("ipt", ctypes.c_int),
-                ("jtile", ctypes.c_int), ("stages", ctypes.c_int)]
+                ("jtile", ctypes.c_int), ("stages", ctypes.c_int),
+                ("unroll", ctypes.c_int), ("minblocks", ctypes.c_int),
+                ("release", ctypes.c_int), ("sums_in_smem", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.threads, self.ipt, self.jtile, self.stages)
+        return tuple(getattr(self, f) for f, _ in self._fields_)
 
     def __repr__(self):
-        return f"nb_tile(threads={self.threads}, ipt={self.ipt}, jtile={self.jtile}, stages={self.stages})"
+        return "nb_tile(" + ", ".join(f"{f}={getattr(self, f)}" for f, _ in self._fields_) + ")"
 
 
 class NBError(RuntimeError):

@@ -405,9 +405,7 @@ nb_status nb_set_tile(nb_ctx *ctx, nb_mode mode, const nb_tile *tile) {
     }
     const bool comp = mode == NB_COMPENSATED;
     for (int k = 0; k < pair_variant_count(comp); ++k) {
-        const nb_tile &t = pair_variant(comp, k)->tile;
-        if (t.threads == tile->threads && t.ipt == tile->ipt && t.jtile == tile->jtile &&
-            t.stages == tile->stages) {
+        if (same_tile(pair_variant(comp, k)->tile, *tile)) {
             ctx->has_override[mi] = true;
             ctx->override_idx[mi] = k;
             return NB_OK;

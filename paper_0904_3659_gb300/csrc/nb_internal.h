@@ -21,7 +21,7 @@ static_assert(sizeof(JPart) == 32, "JPart must be 32 bytes");
 
 // Particle arrays are padded to a multiple of this (>= every i-block and
 // j-tile size) with inert entries (m = 0 at the origin).
-constexpr int64_t kPad = 1024;
+constexpr int64_t kPad = 3072;
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -53,6 +53,12 @@ struct ReduceArgs {
     int maxseg;
     int ib;
 };
+
+inline bool same_tile(const nb_tile &a, const nb_tile &b) {
+    return a.threads == b.threads && a.ipt == b.ipt && a.jtile == b.jtile && a.stages == b.stages &&
+           a.unroll == b.unroll && a.minblocks == b.minblocks && a.release == b.release &&
+           a.sums_in_smem == b.sums_in_smem;
+}
 
 // A compiled pair-kernel shape.
 struct PairVariant {

@@ -110,54 +110,95 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
 
 // ---------------------------------------------------------------------------
 // Persistent pair kernel. See PairArgs for the work split.
-template <int THREADS, int IPT, int JT, int STAGES, bool COMP>
-__global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
+//
+// Template knobs (all searched by the tuner):
+//   THREADS, IPT  CTA size and i-particles per thread (IPT/2 packed pairs)
+//   JT, STAGES    j-tile length and number of shared-memory stages
+//   UNR           unroll factor of the j loop inside a tile
+//   MINB          minimum resident CTAs per SM asked of the register allocator
+//   REL           how a consumed stage is handed back to the producer:
+//                 0: a CTA-wide barrier per tile, after which thread 0 issues
+//                    the copy of the unit STAGES-1 ahead;
+//                 1: no barrier: each warp counts itself out of the stage in a
+//                    shared counter and the last warp to finish issues the
+//                    copy of the unit STAGES ahead into it.
+//   ACCS          where the running sums (and Kahan carries) live between
+//                 tiles: 0 registers, 1 shared memory (one slot per thread,
+//                 touched once per tile; frees 8-16 registers per i-particle)
+//   COMP          Kahan-compensated running sums (NB_COMPENSATED)
+template <int THREADS, int IPT, int JT, int STAGES, int UNR, int MINB, int REL, int ACCS, bool COMP>
+__global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args) {
     static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
     constexpr int P = IPT / 2;
     constexpr int IB = THREADS * IPT;
+    constexpr int NWARPS = THREADS / 32;
     constexpr uint32_t TILE_BYTES = JT * sizeof(JPart);
-    constexpr int UNR = 4;
+    static_assert(THREADS % 32 == 0, "whole warps");
     static_assert(TILE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
     // i-blocks and j-tiles must tile the padded particle array exactly, so
     // that every i and j the kernel touches lies inside it.
     static_assert(kPad % IB == 0 && kPad % JT == 0, "tile sizes must divide the padding");
 
+    // Shared memory: [STAGES j-tiles][running sums if ACCS][barriers][counters]
+    constexpr int NSUM = ACCS ? (COMP ? 2 : 1) * P * 4 * THREADS : 0;  // float2 slots
     extern __shared__ __align__(128) unsigned char smem[];
     JPart *tiles = reinterpret_cast<JPart *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES);
+    float2 *ssum = reinterpret_cast<float2 *>(smem + (size_t)STAGES * TILE_BYTES);
+    float2 *scmp = ssum + P * 4 * THREADS;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES +
+                                                  (size_t)NSUM * sizeof(float2));
+    int *arrivals = reinterpret_cast<int *>(full + STAGES);  // REL 1: warps done per stage
+    int *issued_at = arrivals + STAGES;  // last unit index issued into each stage (-1: none)
+    int *abort_flag = issued_at + STAGES;
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int64_t c = blockIdx.x;
     const int64_t u0 = c * args.units / args.grid;
     const int64_t u1 = (c + 1) * args.units / args.grid;
-    const int64_t count = u1 - u0;
+    const int count = (int)(u1 - u0);
     const int64_t bfirst = u0 / args.njt;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            arrivals[s] = 0;
+            issued_at[s] = -1;
+        }
+        *abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    // Producer state (thread 0): units u0 .. u0+issued-1 have been issued.
-    int64_t issued = 0;
-    auto issue_next = [&]() {
-        const int64_t u = u0 + issued;
-        const int s = (int)(issued % STAGES);
-        if (u != args.fault_unit) {
-            const int64_t jt = u % args.njt;
-            mbar_arrive_expect_tx(&full[s], TILE_BYTES);
-            bulk_g2s(tiles + (size_t)s * JT, args.jp + jt * JT, TILE_BYTES, &full[s]);
-        }
-        ++issued;
+    // Issue the copy of the j-tile of local unit kk into its stage.
+    auto issue = [&](int kk) {
+        const int s = kk % STAGES;
+        const int64_t u = u0 + kk;
+        if (u == args.fault_unit) return;  // test hook: this copy never happens
+        const int64_t jt = u % args.njt;
+        issued_at[s] = kk;
+        mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+        bulk_g2s(tiles + (size_t)s * JT, args.jp + jt * JT, TILE_BYTES, &full[s]);
     };
-    if (tid == 0)
-        while (issued < count && issued < STAGES - 1) issue_next();
+    if (tid == 0) {
+        const int ahead = REL ? STAGES : STAGES - 1;
+        for (int kk = 0; kk < count && kk < ahead; ++kk) issue(kk);
+    }
 
     float2 xi[P], yi[P], zi[P];
     float2 sum[P][4], cmp[P][4];
     const float2 eps2 = splat2(args.eps2);
     const float2 zero2 = splat2(0.f);
+
+    // Running sums: in registers (ACCS 0) or in this thread's shared slots.
+    auto get_sum = [&](int q, int r) { return ACCS ? ssum[(q * 4 + r) * THREADS + tid] : sum[q][r]; };
+    auto get_cmp = [&](int q, int r) { return ACCS ? scmp[(q * 4 + r) * THREADS + tid] : cmp[q][r]; };
+    auto put_sum = [&](int q, int r, float2 v) {
+        if (ACCS) ssum[(q * 4 + r) * THREADS + tid] = v; else sum[q][r] = v;
+    };
+    auto put_cmp = [&](int q, int r, float2 v) {
+        if (ACCS) scmp[(q * 4 + r) * THREADS + tid] = v; else cmp[q][r] = v;
+    };
 
     auto flush = [&](int64_t b) {
         const int64_t seg = b - bfirst;
@@ -165,27 +206,32 @@ __global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int i0 = (2 * q) * THREADS + tid, i1 = i0 + THREADS;
-            dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
-            dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+            const float2 s0 = get_sum(q, 0), s1 = get_sum(q, 1), s2 = get_sum(q, 2), s3 = get_sum(q, 3);
+            dst[i0] = make_float4(s0.x, s1.x, s2.x, s3.x);
+            dst[i1] = make_float4(s0.y, s1.y, s2.y, s3.y);
             if (COMP) {
-                dst[IB + i0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
-                dst[IB + i1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
+                const float2 c0 = get_cmp(q, 0), c1 = get_cmp(q, 1), c2 = get_cmp(q, 2),
+                             c3 = get_cmp(q, 3);
+                dst[IB + i0] = make_float4(c0.x, c1.x, c2.x, c3.x);
+                dst[IB + i1] = make_float4(c0.y, c1.y, c2.y, c3.y);
             }
         }
     };
 
+    int64_t b = u0 / args.njt;
+    int64_t jt = u0 - b * args.njt;
     int64_t cur_b = -1;
     int bad = 0;
-    int64_t k = 0;
-    for (; k < count; ++k) {
-        // Every thread is done with iteration k-1, so its stage may be
-        // refilled; a timeout seen by any thread ends the loop for all.
-        if (__syncthreads_or(bad)) break;
-        if (tid == 0 && issued < count) issue_next();
+    for (int k = 0; k < count; ++k) {
+        if (REL == 0) {
+            // Every thread is done with iteration k-1, so its stage may be
+            // refilled; a timeout seen by any thread ends the loop for all.
+            if (__syncthreads_or(bad)) break;
+            if (tid == 0 && k + STAGES - 1 < count) issue(k + STAGES - 1);
+        } else if (bad || *reinterpret_cast<volatile int *>(abort_flag)) {
+            break;
+        }
 
-        const int64_t u = u0 + k;
-        const int64_t b = u / args.njt;
-        const int64_t jt = u - b * args.njt;
         if (b != cur_b) {
             if (cur_b >= 0) flush(cur_b);
             cur_b = b;
@@ -201,15 +247,16 @@ __global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
                 zi[q] = make_float2(-B0.x, -B1.x);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    sum[q][r] = zero2;
-                    cmp[q][r] = zero2;
+                    put_sum(q, r, zero2);
+                    if (COMP) put_cmp(q, r, zero2);
                 }
             }
         }
 
-        const int s = (int)(k % STAGES);
+        const int s = k % STAGES;
         if (!mbar_wait_bounded(&full[s], (uint32_t)((k / STAGES) & 1), args.wait_ns)) {
             bad = 1;
+            if (REL) atomicOr(abort_flag, 1);
             continue;
         }
         const JPart *T = tiles + (size_t)s * JT;
@@ -233,6 +280,19 @@ __global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
             tile_pass<P, JT, UNR, false>(T, xi, yi, zi, acc, eps2, self0, self1);
         }
 
+        if (REL == 1) {
+            // Hand the stage back: the last warp out issues its next copy.
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const int target = (k / STAGES + 1) * NWARPS;
+                if (atomicAdd(&arrivals[s], 1) == target - 1 && k + STAGES < count) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(k + STAGES);
+                }
+            }
+        }
+
 #pragma unroll
         for (int q = 0; q < P; ++q)
 #pragma unroll
@@ -240,17 +300,23 @@ __global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
                 if (COMP) {
                     // Kahan: the running sum's lost low part is kept in cmp
                     // (true value = sum - cmp).
-                    const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
-                    const float2 t = add2(sum[q][r], y);
-                    cmp[q][r] = add2(add2(t, neg2(sum[q][r])), neg2(y));
-                    sum[q][r] = t;
+                    const float2 s0 = get_sum(q, r);
+                    const float2 y = add2(acc[q][r], neg2(get_cmp(q, r)));
+                    const float2 t = add2(s0, y);
+                    put_cmp(q, r, add2(add2(t, neg2(s0)), neg2(y)));
+                    put_sum(q, r, t);
                 } else {
-                    sum[q][r] = add2(sum[q][r], acc[q][r]);
+                    put_sum(q, r, add2(get_sum(q, r), acc[q][r]));
                 }
             }
+        if (++jt == args.njt) {
+            jt = 0;
+            ++b;
+        }
     }
 
-    bad = __syncthreads_or(bad);
+    // Every warp leaves the loop (a timed-out wait ends it within the limit).
+    bad = __syncthreads_or(bad || *reinterpret_cast<volatile int *>(abort_flag));
     if (!bad) {
         if (cur_b >= 0) flush(cur_b);
         return;
@@ -258,11 +324,10 @@ __global__ void __launch_bounds__(THREADS) pair_kernel(const PairArgs args) {
     if (tid == 0) {
         atomicOr(args.err, kErrTimeout);
         // Let every copy still in flight land before this CTA's shared
-        // memory is released. The unit that failed is k-1 (or the last one).
-        for (int64_t kk = (k > 0 ? k - 1 : 0); kk < issued; ++kk) {
-            if (u0 + kk == args.fault_unit) continue;
-            mbar_wait_bounded(&full[kk % STAGES], (uint32_t)((kk / STAGES) & 1), args.wait_ns);
-        }
+        // memory is released.
+        for (int s = 0; s < STAGES; ++s)
+            if (issued_at[s] >= 0)
+                mbar_wait_bounded(&full[s], (uint32_t)((issued_at[s] / STAGES) & 1), args.wait_ns);
     }
 }
 
@@ -347,38 +412,54 @@ __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed
 
 // ---------------------------------------------------------------------------
 // Launchers and the registry of compiled shapes.
-template <int T, int I, int J, int S, bool C>
+template <int T, int I, int J, int S, int U, int M, int R, int A, bool C>
 static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
-    pair_kernel<T, I, J, S, C><<<grid, T, smem, st>>>(a);
+    pair_kernel<T, I, J, S, U, M, R, A, C><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int S, int J>
+template <int T, int I, int J, int S, int A, bool C>
 constexpr size_t pair_smem() {
-    return (size_t)S * J * sizeof(JPart) + (size_t)S * sizeof(uint64_t);
+    // stages, running sums, their barriers, arrival counters, issue records, abort flag
+    return (size_t)S * J * sizeof(JPart) + (A ? (C ? 2 : 1) * (I / 2) * 4 * T * sizeof(float2) : 0) +
+           (size_t)S * sizeof(uint64_t) + (2 * S + 1) * sizeof(int);
 }
 
-#define NB_VARIANT(T, I, J, S, C) \
-    {{T, I, J, S}, C, (const void *)pair_kernel<T, I, J, S, C>, pair_smem<S, J>(), launch_pair<T, I, J, S, C>}
+#define NB_VARIANT(T, I, J, S, U, M, R, A, C)                                                   \
+    {{T, I, J, S, U, M, R, A}, C, (const void *)pair_kernel<T, I, J, S, U, M, R, A, C>,            \
+     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, C>}
 
-// Plain shapes: the first entries are the defaults for small and large n.
+// Plain shapes: entry 0 is the large-n default, entry 1 the small-n default.
 static const PairVariant kPlain[] = {
-    NB_VARIANT(128, 4, 256, 3, false),  // 0: large-n default
-    NB_VARIANT(64, 2, 64, 4, false),    // 1: small-n default
-    NB_VARIANT(128, 8, 256, 3, false),
-    NB_VARIANT(256, 4, 256, 3, false),
-    NB_VARIANT(128, 4, 512, 2, false),
-    NB_VARIANT(128, 2, 128, 4, false),
-    NB_VARIANT(256, 2, 128, 4, false),
-    NB_VARIANT(64, 4, 128, 4, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 0, 0, false),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, false),
+    NB_VARIANT(128, 8, 512, 3, 8, 1, 0, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 0, 1, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 3, 0, 1, false),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, false),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 1, 1, false),
+    NB_VARIANT(128, 12, 256, 3, 8, 1, 0, 1, false),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 1, 1, false),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, false),
+    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, false),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, false),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, false),
+    NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, false),
 };
 static const PairVariant kComp[] = {
-    NB_VARIANT(128, 4, 256, 3, true),   // 0: large-n default
-    NB_VARIANT(64, 2, 64, 4, true),     // 1: small-n default
-    NB_VARIANT(128, 2, 128, 4, true),
-    NB_VARIANT(256, 4, 256, 3, true),
-    NB_VARIANT(128, 4, 512, 2, true),
-    NB_VARIANT(256, 2, 128, 4, true),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, true),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 0, 1, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, true),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, true),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, true),
+    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, true),
+    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, true),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, true),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, true),
 };
 #undef NB_VARIANT
 
@@ -394,8 +475,7 @@ const PairVariant *pair_variant(bool comp, int idx) {
 const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
     for (int k = 0; k < pair_variant_count(comp); ++k) {
         const nb_tile &v = pair_variant(comp, k)->tile;
-        if (v.threads == t.threads && v.ipt == t.ipt && v.jtile == t.jtile && v.stages == t.stages)
-            return pair_variant(comp, k);
+        if (same_tile(v, t)) return pair_variant(comp, k);
     }
     return nullptr;
 }

@@ -46,7 +46,8 @@ def test_host_only_calls(lib):
     assert len(tiles) >= 4
     for t in tiles + lib.nb_list_tiles(lib.NB_COMPENSATED):
         ib = t.threads * t.ipt
-        assert t.ipt % 2 == 0 and 1024 % ib == 0 and 1024 % t.jtile == 0 and t.stages >= 2
+        assert t.ipt % 2 == 0 and 3072 % ib == 0 and 3072 % t.jtile == 0 and t.stages >= 2
+        assert t.threads % 32 == 0 and t.release in (0, 1) and t.unroll >= 1
         assert (t.jtile * 32) % 16 == 0
 
 

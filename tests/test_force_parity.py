@@ -201,17 +201,20 @@ def test_argument_errors(nb, ctx):
     # n == 0 is a valid no-op, even with NULL pointers.
     nb.nb_force(ctx, None, None, 0, 0.1, None, None)
     with pytest.raises(nb.NBError) as e:
-        nb.nb_set_tile(ctx, 0, (96, 3, 100, 2))
+        nb.nb_set_tile(ctx, 0, (96, 3, 100, 2, 4, 1, 0, 0))
     assert e.value.status == nb.NB_ERR_ARG
 
 
-def test_bounded_wait_reports_timeout_and_context_survives(nb, ctx, oracle_mod):
+@pytest.mark.parametrize("release", [0, 1])
+def test_bounded_wait_reports_timeout_and_context_survives(nb, ctx, oracle_mod, release):
     # The producer skips the copy of one work unit, so the consumers' bounded
     # wait (0.2 s here) runs out; the kernel records a timeout and returns,
     # and nb_synchronize reports it. Nothing hangs or faults, and the next
-    # call on the same context is correct.
+    # call on the same context is correct. Both stage-release schemes.
     x32, m32 = plummer32(4096, seed=0)
     eps = np.float32(0.01)
+    tile = [t for t in nb.nb_list_tiles(0) if t.release == release][0]
+    nb.nb_set_tile(ctx, 0, tile)
     nb.nb_debug_set_fault(ctx, 3, 200_000_000)
     try:
         import torch
@@ -226,7 +229,10 @@ def test_bounded_wait_reports_timeout_and_context_survives(nb, ctx, oracle_mod):
         assert e.value.status == nb.NB_ERR_TIMEOUT
     finally:
         nb.nb_debug_set_fault(ctx, -1, 0)
-    a, p = gpu_force(nb, ctx, x32, m32, eps, 0)
+    try:
+        a, p = gpu_force(nb, ctx, x32, m32, eps, 0)
+    finally:
+        nb.nb_set_tile(ctx, 0, None)
     ra, rp, ramag = oracle_mod.force(x32, m32, eps)
     ea, ep = rel_errors(a, p, ra, rp, ramag)
     assert ea.max() <= 1e-5 and ep.max() <= 1e-5
