@@ -78,7 +78,10 @@ typedef struct nb_ctx nb_ctx;
  * how a consumed stage is refilled (0: CTA barrier per tile; 1: the last
  * warp to finish the tile issues the next copy, no barrier), `sums_in_smem`
  * whether the running sums between tiles live in shared memory (1) or in
- * registers (0). */
+ * registers (0), and `packed` a bit mask of the interaction's operation
+ * groups that run as packed FP32x2 instructions (1 difference, 2 distance,
+ * 4 Newton step, 8 potential term, 16 force weight, 32 force accumulation;
+ * the others run as scalar FP32; every mask gives bit-identical results). */
 typedef struct nb_tile {
     int threads;
     int ipt;
@@ -88,6 +91,7 @@ typedef struct nb_tile {
     int minblocks;
     int release;
     int sums_in_smem;
+    int packed;
 } nb_tile;
 
 /* Create a context on CUDA device `device`. *out receives the handle. */

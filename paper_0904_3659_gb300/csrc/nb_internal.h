@@ -57,7 +57,7 @@ struct ReduceArgs {
 inline bool same_tile(const nb_tile &a, const nb_tile &b) {
     return a.threads == b.threads && a.ipt == b.ipt && a.jtile == b.jtile && a.stages == b.stages &&
            a.unroll == b.unroll && a.minblocks == b.minblocks && a.release == b.release &&
-           a.sums_in_smem == b.sums_in_smem;
+           a.sums_in_smem == b.sums_in_smem && a.packed == b.packed;
 }
 
 // A compiled pair-kernel shape.

@@ -66,7 +66,27 @@ __global__ void pack_f32_kernel(const float *__restrict__ x, const float *__rest
 // In a diagonal tile (DIAG) the j == i term is removed by zeroing the mass
 // lane of the thread's own particle; self0/self1 give, per pair, the tile
 // position of the thread's own i (outside [0, JT) when it is not here).
-template <int P, int JT, int UNR, bool DIAG>
+// Operation groups of one interaction. Bit g of a MIX mask set: the group
+// runs as packed FP32x2 instructions; clear: as two scalar FP32 instructions
+// (same IEEE round-to-nearest operations, so every mask gives bit-identical
+// results). Mixing trades issue slots (packed: one per two lanes) against
+// the lower sustained pipe rate of packed instructions.
+enum : int { kMixD = 1, kMixS = 2, kMixN = 4, kMixQ = 8, kMixW = 16, kMixA = 32, kMixAll = 63 };
+
+template <bool PK>
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) {
+    return PK ? add2(a, b) : make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+template <bool PK>
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) {
+    return PK ? mul2(a, b) : make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+template <bool PK>
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+    return PK ? fma2(a, b, c) : make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+
+template <int P, int JT, int UNR, bool DIAG, int MIX>
 __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const float2 (&xi)[P],
                                           const float2 (&yi)[P], const float2 (&zi)[P],
                                           float2 (&acc)[P][4], const float2 eps2,
@@ -82,28 +102,30 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
         const float2 hmj = make_float2(B.z, B.w);
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const float2 dx = add2(xi[q], nxj);
-            const float2 dy = add2(yi[q], nyj);
-            const float2 dz = add2(zi[q], nzj);
-            float2 s = fma2(dx, dx, eps2);
-            s = fma2(dy, dy, s);
-            s = fma2(dz, dz, s);
+            constexpr bool PD = MIX & kMixD, PS = MIX & kMixS, PN = MIX & kMixN;
+            constexpr bool PQ = MIX & kMixQ, PW = MIX & kMixW, PA = MIX & kMixA;
+            const float2 dx = vadd<PD>(xi[q], nxj);
+            const float2 dy = vadd<PD>(yi[q], nyj);
+            const float2 dz = vadd<PD>(zi[q], nzj);
+            float2 s = vfma<PS>(dx, dx, eps2);
+            s = vfma<PS>(dy, dy, s);
+            s = vfma<PS>(dz, dz, s);
             const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
-            const float2 y2 = mul2(y, y);
-            const float2 t = fma2(s, y2, m3);
-            const float2 u = mul2(y, t);
+            const float2 y2 = vmul<PN>(y, y);
+            const float2 t = vfma<PN>(s, y2, m3);
+            const float2 u = vmul<PN>(y, t);
             float2 hm = hmj;
             if (DIAG) {
                 if (jj == self0[q]) hm.x = 0.f;
                 if (jj == self1[q]) hm.y = 0.f;
             }
-            const float2 qv = mul2(hm, u);
-            acc[q][3] = add2(acc[q][3], qv);
-            const float2 u2 = mul2(u, u);
-            const float2 w = mul2(qv, u2);
-            acc[q][0] = fma2(w, dx, acc[q][0]);
-            acc[q][1] = fma2(w, dy, acc[q][1]);
-            acc[q][2] = fma2(w, dz, acc[q][2]);
+            const float2 qv = vmul<PQ>(hm, u);
+            acc[q][3] = vadd<PQ>(acc[q][3], qv);
+            const float2 u2 = vmul<PW>(u, u);
+            const float2 w = vmul<PW>(qv, u2);
+            acc[q][0] = vfma<PA>(w, dx, acc[q][0]);
+            acc[q][1] = vfma<PA>(w, dy, acc[q][1]);
+            acc[q][2] = vfma<PA>(w, dz, acc[q][2]);
         }
     }
 }
@@ -125,8 +147,10 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
 //   ACCS          where the running sums (and Kahan carries) live between
 //                 tiles: 0 registers, 1 shared memory (one slot per thread,
 //                 touched once per tile; frees 8-16 registers per i-particle)
+//   MIX           which op groups of an interaction run packed (see kMix*)
 //   COMP          Kahan-compensated running sums (NB_COMPENSATED)
-template <int THREADS, int IPT, int JT, int STAGES, int UNR, int MINB, int REL, int ACCS, bool COMP>
+template <int THREADS, int IPT, int JT, int STAGES, int UNR, int MINB, int REL, int ACCS, int MIX,
+          bool COMP>
 __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args) {
     static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
     constexpr int P = IPT / 2;
@@ -275,9 +299,9 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
                 self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
                 self1[q] = self0[q] + THREADS;
             }
-            tile_pass<P, JT, 1, true>(T, xi, yi, zi, acc, eps2, self0, self1);
+            tile_pass<P, JT, 1, true, MIX>(T, xi, yi, zi, acc, eps2, self0, self1);
         } else {
-            tile_pass<P, JT, UNR, false>(T, xi, yi, zi, acc, eps2, self0, self1);
+            tile_pass<P, JT, UNR, false, MIX>(T, xi, yi, zi, acc, eps2, self0, self1);
         }
 
         if (REL == 1) {
@@ -412,9 +436,9 @@ __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed
 
 // ---------------------------------------------------------------------------
 // Launchers and the registry of compiled shapes.
-template <int T, int I, int J, int S, int U, int M, int R, int A, bool C>
+template <int T, int I, int J, int S, int U, int M, int R, int A, int X, bool C>
 static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
-    pair_kernel<T, I, J, S, U, M, R, A, C><<<grid, T, smem, st>>>(a);
+    pair_kernel<T, I, J, S, U, M, R, A, X, C><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -425,41 +449,37 @@ constexpr size_t pair_smem() {
            (size_t)S * sizeof(uint64_t) + (2 * S + 1) * sizeof(int);
 }
 
-#define NB_VARIANT(T, I, J, S, U, M, R, A, C)                                                   \
-    {{T, I, J, S, U, M, R, A}, C, (const void *)pair_kernel<T, I, J, S, U, M, R, A, C>,            \
-     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, C>}
+#define NB_VARIANT(T, I, J, S, U, M, R, A, X, C)                                                \
+    {{T, I, J, S, U, M, R, A, X}, C, (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, C>,      \
+     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, C>}
 
 // Plain shapes: entry 0 is the large-n default, entry 1 the small-n default.
+// (Measured on GB300 at N = 2^18 and 2^20: the all-packed mask 63 beats every
+// scalar or mixed mask; IPT 6-12 with ~2 warps per scheduler are fastest.)
 static const PairVariant kPlain[] = {
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 0, 0, false),
-    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, false),
-    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, false),
-    NB_VARIANT(128, 8, 512, 3, 8, 1, 0, 0, false),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, false),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 0, 1, false),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, false),
-    NB_VARIANT(128, 8, 256, 3, 8, 3, 0, 1, false),
-    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, false),
-    NB_VARIANT(128, 12, 256, 3, 4, 1, 1, 1, false),
-    NB_VARIANT(128, 12, 256, 3, 8, 1, 0, 1, false),
-    NB_VARIANT(128, 6, 256, 3, 8, 1, 1, 1, false),
-    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, false),
-    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, false),
-    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, false),
-    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, false),
-    NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 63, false),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, false),
+    NB_VARIANT(128, 8, 512, 3, 8, 1, 0, 0, 63, false),
+    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, 63, false),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, false),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 1, 1, 63, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 28, false),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, false),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, false),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, false),
+    NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, 63, false),
 };
 static const PairVariant kComp[] = {
-    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, true),
-    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, true),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 0, 1, true),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, true),
-    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, true),
-    NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, true),
-    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, true),
-    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, true),
-    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, true),
-    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, true),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, true),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, true),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, true),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 0, true),
+    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, 63, true),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, true),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, true),
 };
 #undef NB_VARIANT
 

@@ -201,7 +201,7 @@ def test_argument_errors(nb, ctx):
     # n == 0 is a valid no-op, even with NULL pointers.
     nb.nb_force(ctx, None, None, 0, 0.1, None, None)
     with pytest.raises(nb.NBError) as e:
-        nb.nb_set_tile(ctx, 0, (96, 3, 100, 2, 4, 1, 0, 0))
+        nb.nb_set_tile(ctx, 0, (96, 3, 100, 2, 4, 1, 0, 0, 63))
     assert e.value.status == nb.NB_ERR_ARG
 
 
