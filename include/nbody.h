@@ -103,7 +103,8 @@ void nb_destroy(nb_ctx *ctx);
 
 /* Message describing the last failure on this context ("" if none). The
  * pointer stays valid until the next call on the context. NULL ctx gives the
- * message of the last failed nb_create. */
+ * message of the last failed call without a context on this host thread
+ * (nb_create, nb_force_noalloc). */
 const char *nb_last_error(const nb_ctx *ctx);
 
 /* Static name of a status code. */
@@ -189,6 +190,36 @@ nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *
  */
 nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
                        const float *ga, const float *gp, float *gx, float *gm, void *stream);
+
+/*
+ * nb_force for callers that may not allocate device memory. (This entry
+ * point is an engineering addition; the paper has no counterpart.)
+ *
+ * Some callers cannot call cudaMalloc where they need forces: their device
+ * memory is entirely owned by a pool or framework allocator, they run in a
+ * loop that cannot afford the device-wide synchronisation an allocation can
+ * trigger, or they are plug-ins that are handed buffers but not allowed to
+ * allocate. This call needs no context and allocates nothing: its scratch
+ * (packed particles and partial sums, plus an error word) is a fixed 16 MiB
+ * array inside the library's device image, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ *   x, m, a, p, eps  as in nb_force (FP32 DEVICE arrays of the current
+ *                    device; plain arithmetic, NB_PLAIN results)
+ *   n                at most 65536; larger n, or a device whose work split
+ *                    would not fit the array, is rejected with NB_ERR_ARG
+ *                    and a message (nb_last_error(NULL))
+ *   stream           cudaStream_t as void* (NULL = legacy default stream)
+ * The call waits for `stream` before returning and reports a bounded-wait
+ * timeout as NB_ERR_TIMEOUT. Its first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture. All calls share the one array, which
+ * keeps the previous call's contents (everything that is read is rewritten
+ * first): calls that overlap on the GPU, from several host threads or on
+ * several streams, race on it and must be serialised by the caller.
+ */
+nb_status nb_force_noalloc(const float *x, const float *m, int64_t n, float eps, float *a, float *p,
+                           void *stream);
 
 /* Wait for `stream` and report device-side errors recorded by this context's
  * kernels since the last check (NB_ERR_TIMEOUT if a bounded wait ran out). */

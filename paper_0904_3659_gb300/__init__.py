@@ -27,7 +27,7 @@ __all__ = [
     "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_step", "nb_energy",
     "nb_force_vjp", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_list_tiles",
     "nb_autotune", "nb_timing_enable", "nb_timing_read", "nb_timing_reset",
-    "nb_debug_set_fault", "force",
+    "nb_debug_set_fault", "nb_force_noalloc", "force",
 ]
 
 NB_OK = 0
@@ -96,6 +96,7 @@ _SIGNATURES = {
     "nb_timing_read": (_c.c_int, [_P, _c.c_int, _c.POINTER(_c.c_double), _c.POINTER(_I64)]),
     "nb_timing_reset": (_c.c_int, [_P]),
     "nb_debug_set_fault": (_c.c_int, [_P, _I64, _I64]),
+    "nb_force_noalloc": (_c.c_int, [_P, _P, _I64, _c.c_float, _P, _P, _P]),
 }
 exported_symbols = tuple(_SIGNATURES)
 
@@ -231,6 +232,12 @@ def nb_force_vjp(ctx, x, m, n, eps, ga, gp, gx, gm, stream=None):
     _check(ctx, library().nb_force_vjp(ctx.handle, _addr(x), _addr(m), int(n), float(eps),
                                        _addr(ga), _addr(gp), _addr(gx), _addr(gm),
                                        _stream(stream)))
+
+
+def nb_force_noalloc(x, m, n, eps, a, p, stream=None):
+    """Allocation-free nb_force (no context; n <= 65536; waits for the stream)."""
+    _check(None, library().nb_force_noalloc(_addr(x), _addr(m), int(n), float(eps), _addr(a),
+                                            _addr(p), _stream(stream)))
 
 
 def nb_synchronize(ctx, stream=None):

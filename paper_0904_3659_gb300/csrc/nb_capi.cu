@@ -15,7 +15,9 @@ using namespace nbk;
 
 namespace {
 
-std::string g_create_error;  // message of the last failed nb_create
+// Message of the last failed call that has no context (nb_create,
+// nb_force_noalloc), per host thread.
+thread_local std::string g_create_error;
 
 enum KernelClass { K_PACK = 0, K_PAIR = 1, K_REDUCE = 2, K_LEAPFROG = 3, K_BATCHED = 4, K_VJP = 5,
                    K_COUNT = 8 };
@@ -99,6 +101,8 @@ nbx::TimedLaunch::~TimedLaunch() {
 }
 
 namespace nbx {
+
+void set_global_error(const std::string &m) { g_create_error = m; }
 
 nb_status fail(nb_ctx *ctx, nb_status st, const std::string &m) {
     if (ctx) ctx->msg = m;

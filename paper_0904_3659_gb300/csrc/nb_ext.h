@@ -34,6 +34,8 @@ class TimedLaunch {
 };
 
 nb_status fail(nb_ctx *ctx, nb_status st, const std::string &m);
+// Message returned by nb_last_error(NULL) (calls without a context).
+void set_global_error(const std::string &m);
 nb_status cuda_fail(nb_ctx *ctx, cudaError_t e, const char *what);
 nb_status check_common(nb_ctx *ctx, int64_t n, float eps, int mode);
 
