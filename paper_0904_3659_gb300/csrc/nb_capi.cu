@@ -119,6 +119,11 @@ int ctx_device(const nb_ctx *ctx) { return ctx->device; }
 int ctx_sm_count(const nb_ctx *ctx) { return ctx->sm_count; }
 int *ctx_err_word(nb_ctx *ctx) { return ctx->d_err; }
 ExtState &ctx_ext(nb_ctx *ctx) { return ctx->ext; }
+bool ctx_set_timing(nb_ctx *ctx, bool on) {
+    const bool prev = ctx->timing;
+    ctx->timing = on;
+    return prev;
+}
 uint64_t ctx_wait_ns(const nb_ctx *ctx) { return ctx->wait_ns; }
 
 cudaError_t ensure_buffer(void **ptr, size_t *cap, size_t bytes) {

@@ -1,0 +1,277 @@
+// nb_dynamics.cu -- leap-frog integration (Fujiwara & Nakasato,
+// arXiv:0904.3659, Section "Method", Eqs. (1)-(3)) and total energy, with the
+// state (x, v) in FP64 on the device and the force from the FP32 pair kernel.
+//
+// One step (kick-drift-kick, the seven-step algorithm of Section "Method"):
+//   v <- v + dt/2 g(x)       Eq. (1)
+//   x <- x + dt v            Eq. (2) (x + v dt + g dt^2/2 with the new v)
+//   g(x) from Eq. (gravity)  (g = -a: Eq. (gravity) has the sign of a repulsion)
+//   v <- v + dt/2 g(x)       Eq. (3)
+// The back kick of step k and the front kick of step k+1 use the same g and
+// run in one kernel as two separate FP64 additions (identical rounding to
+// running them apart), fused with the drift and the FP32 packing of the new
+// positions. Steps after the first are replayed from a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "nb_device.cuh"
+#include "nb_ext.h"
+#include "nb_internal.h"
+
+namespace nbk {
+
+// Pack FP64 positions (rounded to FP32) and FP32 masses into JPart.
+__device__ __forceinline__ void pack_one(JPart *jp, int64_t i, double px, double py, double pz,
+                                         float mi) {
+    const float fx = (float)px, fy = (float)py, fz = (float)pz;
+    const float hm = -0.5f * mi;
+    float4 *dst = reinterpret_cast<float4 *>(jp + i);
+    dst[0] = make_float4(-fx, -fx, -fy, -fy);
+    dst[1] = make_float4(-fz, -fz, hm, hm);
+}
+
+__global__ void pack_f64_kernel(const double *__restrict__ x, const float *__restrict__ m,
+                                int64_t n, int64_t npad, JPart *__restrict__ jp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    if (i < n)
+        pack_one(jp, i, x[3 * i], x[3 * i + 1], x[3 * i + 2], m[i]);
+    else
+        pack_one(jp, i, 0.0, 0.0, 0.0, 0.f);
+}
+
+// v += dt/2 g (back kick, if kick_back), v += dt/2 g (front kick),
+// x += dt v, then pack x. g = -a.
+__global__ void kick_drift_pack_kernel(double *__restrict__ x, double *__restrict__ v,
+                                       const float *__restrict__ a, const float *__restrict__ m,
+                                       int64_t n, int64_t npad, double dt, int kick_back,
+                                       JPart *__restrict__ jp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    if (i >= n) {
+        pack_one(jp, i, 0.0, 0.0, 0.0, 0.f);
+        return;
+    }
+    const double h = 0.5 * dt;
+    double xn[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double g = -(double)a[3 * i + c];
+        double vc = v[3 * i + c];
+        if (kick_back) vc = vc + h * g;  // Eq. (3) of the previous step
+        vc = vc + h * g;                 // Eq. (1)
+        const double xc = x[3 * i + c] + dt * vc;  // Eq. (2)
+        v[3 * i + c] = vc;
+        x[3 * i + c] = xc;
+        xn[c] = xc;
+    }
+    pack_one(jp, i, xn[0], xn[1], xn[2], m[i]);
+}
+
+__global__ void kick_kernel(double *__restrict__ v, const float *__restrict__ a, int64_t n,
+                            double dt) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    v[k] = v[k] + (0.5 * dt) * (-(double)a[k]);  // Eq. (3)
+}
+
+// Energy: per-block sums of K = 1/2 m |v|^2 and W = -1/2 m p in a fixed
+// tree order, then one block adds the block sums in order.
+constexpr int kEnergyThreads = 256;
+
+__global__ void energy_partial_kernel(const double *__restrict__ v, const float *__restrict__ m,
+                                      const float *__restrict__ p, int64_t n,
+                                      double2 *__restrict__ block_sums) {
+    __shared__ double sk[kEnergyThreads], sw[kEnergyThreads];
+    const int t = threadIdx.x;
+    double k = 0.0, w = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kEnergyThreads + t; i < n;
+         i += (int64_t)gridDim.x * kEnergyThreads) {
+        const double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
+        const double mi = m[i];
+        k += 0.5 * mi * (vx * vx + vy * vy + vz * vz);
+        w += -0.5 * mi * (double)p[i];
+    }
+    sk[t] = k;
+    sw[t] = w;
+    __syncthreads();
+    for (int s = kEnergyThreads / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            sk[t] += sk[t + s];
+            sw[t] += sw[t + s];
+        }
+        __syncthreads();
+    }
+    if (t == 0) block_sums[blockIdx.x] = make_double2(sk[0], sw[0]);
+}
+
+__global__ void energy_final_kernel(const double2 *__restrict__ block_sums, int nblocks,
+                                    double2 *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double k = 0.0, w = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        k += block_sums[b].x;
+        w += block_sums[b].y;
+    }
+    *out = make_double2(k, w);
+}
+
+}  // namespace nbk
+
+using namespace nbk;
+using namespace nbx;
+
+namespace {
+
+enum Slot { S_JP = 0, S_A = 1, S_P = 2, S_EBLK = 3, S_EOUT = 4 };
+
+void *slot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
+
+nb_status ensure_slot(nb_ctx *ctx, int k, size_t bytes) {
+    ExtState &s = ctx_ext(ctx);
+    cudaError_t e = ensure_buffer(&s.buf[k], &s.cap[k], bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
+    return NB_OK;
+}
+
+unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// Reserve everything one force evaluation from packed FP64 positions needs.
+nb_status reserve_force(nb_ctx *ctx, int64_t n, bool comp) {
+    const PairVariant &v = choose_variant(ctx, n, comp);
+    const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
+    return ensure_slot(ctx, S_JP, (size_t)plan.npad * sizeof(JPart));
+}
+
+int64_t padded(int64_t n) { return round_up(std::max<int64_t>(n, 1), kPad); }
+
+// Enqueue the steps 1 .. nsteps-1 body: fused kicks+drift+pack, force.
+nb_status steady_step(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
+                      int64_t n, float eps, double dt, bool comp, cudaStream_t st) {
+    JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
+    kick_drift_pack_kernel<<<blocks_for(padded(n), 256), 256, 0, st>>>(x, v, a, m, n, padded(n), dt,
+                                                                        1, jp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "leap-frog update launch");
+    return run_force(ctx, nullptr, nullptr, jp, n, eps, a, p, comp, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
+                           int64_t n, float eps, double dt, int nsteps, int a_valid, nb_mode mode,
+                           void *stream) {
+    if (!ctx) return NB_ERR_ARG;
+    nb_status st = check_common(ctx, n, eps, mode);
+    if (st != NB_OK) return st;
+    if (nsteps < 0) return fail(ctx, NB_ERR_ARG, "nsteps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ctx, NB_ERR_ARG, "dt must be finite");
+    if (n == 0) return NB_OK;
+    if (!x || !v || !m || !a) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    DeviceGuard g(ctx_device(ctx));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool comp = mode == NB_COMPENSATED;
+
+    // Scratch first (allocation never happens inside the captured graph).
+    if ((st = reserve_force(ctx, n, comp)) != NB_OK) return st;
+    if ((st = nb_reserve(ctx, n, mode)) != NB_OK) return st;
+    float *pbuf = p;
+    if (!pbuf) {
+        if ((st = ensure_slot(ctx, S_P, (size_t)n * sizeof(float))) != NB_OK) return st;
+        pbuf = static_cast<float *>(slot(ctx, S_P));
+    }
+    JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
+    cudaError_t e;
+
+    if (!a_valid) {
+        pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "pack launch");
+        if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, a, pbuf, comp, s)) != NB_OK) return st;
+    }
+    if (nsteps == 0) return NB_OK;
+
+    // Step 0: front kick + drift + pack, force.
+    kick_drift_pack_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, v, a, m, n, padded(n), dt, 0,
+                                                                      jp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "leap-frog update launch");
+    if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, a, pbuf, comp, s)) != NB_OK) return st;
+
+    // Steps 1 .. nsteps-1: the same kernels with the same arguments each
+    // step, so they are captured once into a graph and replayed (not on the
+    // legacy default stream, which cannot be captured).
+    const int rest = nsteps - 1;
+    if (rest >= 2 && s != nullptr) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
+        const bool timing = ctx_set_timing(ctx, false);  // no event nodes in the graph
+        nb_status cst = steady_step(ctx, x, v, m, a, pbuf, n, eps, dt, comp, s);
+        ctx_set_timing(ctx, timing);
+        e = cudaStreamEndCapture(s, &graph);
+        if (cst != NB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cst;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+        for (int k = 0; k < rest && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    } else {
+        for (int k = 0; k < rest; ++k)
+            if ((st = steady_step(ctx, x, v, m, a, pbuf, n, eps, dt, comp, s)) != NB_OK) return st;
+    }
+    // Final back kick, Eq. (3).
+    kick_kernel<<<blocks_for(3 * n, 256), 256, 0, s>>>(v, a, n, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "kick launch");
+    return NB_OK;
+}
+
+nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *m, int64_t n,
+                    float eps, double *out_kw, nb_mode mode, void *stream) {
+    if (!ctx) return NB_ERR_ARG;
+    nb_status st = check_common(ctx, n, eps, mode);
+    if (st != NB_OK) return st;
+    if (!out_kw) return fail(ctx, NB_ERR_ARG, "out_kw is NULL");
+    if (n == 0) {
+        out_kw[0] = out_kw[1] = 0.0;
+        return NB_OK;
+    }
+    if (!x || !v || !m) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    DeviceGuard g(ctx_device(ctx));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool comp = mode == NB_COMPENSATED;
+    if ((st = reserve_force(ctx, n, comp)) != NB_OK) return st;
+    if ((st = ensure_slot(ctx, S_A, (size_t)3 * n * sizeof(float))) != NB_OK) return st;
+    if ((st = ensure_slot(ctx, S_P, (size_t)n * sizeof(float))) != NB_OK) return st;
+    const int nblk = (int)std::min<int64_t>(1024, (n + kEnergyThreads - 1) / kEnergyThreads);
+    if ((st = ensure_slot(ctx, S_EBLK, (size_t)nblk * sizeof(double2))) != NB_OK) return st;
+    if ((st = ensure_slot(ctx, S_EOUT, sizeof(double2))) != NB_OK) return st;
+    JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
+    float *abuf = static_cast<float *>(slot(ctx, S_A));
+    float *pbuf = static_cast<float *>(slot(ctx, S_P));
+    pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pack launch");
+    if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, abuf, pbuf, comp, s)) != NB_OK) return st;
+    double2 *blk = static_cast<double2 *>(slot(ctx, S_EBLK));
+    double2 *out = static_cast<double2 *>(slot(ctx, S_EOUT));
+    energy_partial_kernel<<<nblk, kEnergyThreads, 0, s>>>(v, m, pbuf, n, blk);
+    energy_final_kernel<<<1, 32, 0, s>>>(blk, nblk, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "energy launch");
+    double2 host{};
+    e = cudaMemcpyAsync(&host, out, sizeof(double2), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "energy read");
+    if ((st = nb_synchronize(ctx, stream)) != NB_OK) return st;
+    out_kw[0] = host.x;
+    out_kw[1] = host.y;
+    return NB_OK;
+}
+
+}  // extern "C"

@@ -12,18 +12,6 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *, const float *, const int6
     return fail(ctx, NB_ERR_NOT_IMPLEMENTED, "nb_force_batched is not built yet");
 }
 
-nb_status nb_leapfrog_step(nb_ctx *ctx, double *, double *, const float *, float *, float *, int64_t,
-                           float, double, int, int, nb_mode, void *) {
-    if (!ctx) return NB_ERR_ARG;
-    return fail(ctx, NB_ERR_NOT_IMPLEMENTED, "nb_leapfrog_step is not built yet");
-}
-
-nb_status nb_energy(nb_ctx *ctx, const double *, const double *, const float *, int64_t, float,
-                    double *, nb_mode, void *) {
-    if (!ctx) return NB_ERR_ARG;
-    return fail(ctx, NB_ERR_NOT_IMPLEMENTED, "nb_energy is not built yet");
-}
-
 nb_status nb_force_vjp(nb_ctx *ctx, const float *, const float *, int64_t, float, const float *,
                        const float *, float *, float *, void *) {
     if (!ctx) return NB_ERR_ARG;
