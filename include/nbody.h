@@ -147,11 +147,28 @@ nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode);
  *   eps           [n_clusters] FP32 DEVICE array of per-cluster softening
  *   n_total       offsets[n_clusters] (the total particle count)
  * Asynchronous. Offsets and eps are not read back to the host: the caller
- * guarantees they are valid (eps > 0, finite).
+ * guarantees eps > 0 and finite; offsets that do not start at 0, decrease,
+ * or do not end at n_total are detected on the device, nothing is read or
+ * written, and the next nb_synchronize returns NB_ERR_ARG. Work items are (cluster, block of 128 i-particles),
+ * taken from a device queue by one persistent launch, largest clusters first;
+ * each item is summed by one CTA in a fixed order (bit-reproducible).
  */
 nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const int64_t *offsets,
                            int64_t n_clusters, int64_t n_total, const float *eps,
                            float *a, float *p, nb_mode mode, void *stream);
+
+/*
+ * nb_leapfrog_step for a batch of independent clusters (as nb_force_batched):
+ * x, v FP64 device [n_total][3] in/out; m, eps, offsets as in
+ * nb_force_batched; a [n_total][3] FP32 device, in (if a_valid) / out;
+ * p [n_total] FP32 device, out. One persistent pair launch per step; steps
+ * after the first are replayed from a CUDA graph when `stream` is not the
+ * legacy default stream. Asynchronous.
+ */
+nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const float *m,
+                                   const int64_t *offsets, int64_t n_clusters, int64_t n_total,
+                                   const float *eps, float *a, float *p, double dt, int nsteps,
+                                   int a_valid, nb_mode mode, void *stream);
 
 /*
  * nsteps kick-drift-kick leap-frog steps, Eqs. (1)-(3) of Section "Method",

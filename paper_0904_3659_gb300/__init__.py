@@ -24,7 +24,7 @@ __all__ = [
     "NB_ERR_NOT_IMPLEMENTED", "NB_PLAIN", "NB_COMPENSATED", "NBError", "nb_tile",
     "library", "library_path", "exported_symbols", "Context",
     "nb_create", "nb_destroy", "nb_last_error", "nb_status_string", "nb_force",
-    "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_step", "nb_energy",
+    "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_batched_step", "nb_leapfrog_step", "nb_energy",
     "nb_force_vjp", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_list_tiles",
     "nb_autotune", "nb_timing_enable", "nb_timing_read", "nb_timing_reset",
     "nb_debug_set_fault", "nb_force_noalloc", "force",
@@ -84,6 +84,8 @@ _SIGNATURES = {
     "nb_force_batched": (_c.c_int, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P, _c.c_int, _P]),
     "nb_leapfrog_step": (_c.c_int, [_P, _P, _P, _P, _P, _P, _I64, _c.c_float, _c.c_double,
                                     _c.c_int, _c.c_int, _c.c_int, _P]),
+    "nb_leapfrog_batched_step": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _I64, _P, _P, _P,
+                                            _c.c_double, _c.c_int, _c.c_int, _c.c_int, _P]),
     "nb_energy": (_c.c_int, [_P, _P, _P, _P, _I64, _c.c_float, _P, _c.c_int, _P]),
     "nb_force_vjp": (_c.c_int, [_P, _P, _P, _I64, _c.c_float, _P, _P, _P, _P, _P]),
     "nb_synchronize": (_c.c_int, [_P, _P]),
@@ -219,6 +221,14 @@ def nb_leapfrog_step(ctx, x, v, m, a, p, n, eps, dt, nsteps, a_valid, mode=NB_PL
     _check(ctx, library().nb_leapfrog_step(ctx.handle, _addr(x), _addr(v), _addr(m), _addr(a),
                                            _addr(p), int(n), float(eps), float(dt), int(nsteps),
                                            int(a_valid), int(mode), _stream(stream)))
+
+
+def nb_leapfrog_batched_step(ctx, x, v, m, offsets, n_clusters, n_total, eps, a, p, dt, nsteps,
+                             a_valid, mode=NB_PLAIN, stream=None):
+    _check(ctx, library().nb_leapfrog_batched_step(
+        ctx.handle, _addr(x), _addr(v), _addr(m), _addr(offsets), int(n_clusters), int(n_total),
+        _addr(eps), _addr(a), _addr(p), float(dt), int(nsteps), int(a_valid), int(mode),
+        _stream(stream)))
 
 
 def nb_energy(ctx, x, v, m, n, eps, mode=NB_PLAIN, stream=None):

@@ -1,0 +1,581 @@
+// nb_batched.cu -- Eq. (gravity) (Fujiwara & Nakasato, arXiv:0904.3659,
+// Section "Introduction") for many independent clusters in one persistent
+// launch, and the leap-frog of Section "Method" over such a batch.
+//
+// Layout: the clusters, concatenated by the caller, are packed into a padded
+// copy in which every cluster starts on a multiple of kClusterPad particles
+// and is padded with inert entries (m = 0), so every j-tile and i-block lies
+// inside one cluster. Work item = (cluster, i-block); a one-block planning
+// kernel lists the items grouped by the cluster's padded size, largest first
+// (close to longest-processing-time order), and the pair kernel's CTAs pop
+// items from an atomic counter. Each item is summed entirely by one CTA in a
+// fixed order, so the results do not depend on which CTA pops what.
+#include <algorithm>
+#include <cmath>
+
+#include "nb_device.cuh"
+#include "nb_ext.h"
+#include "nb_internal.h"
+#include "nb_tile.cuh"
+
+namespace nbk {
+using namespace nbdev;
+
+constexpr int kClusterPad = 128;  // >= every batched i-block and j-tile
+constexpr int kPlanThreads = 1024;
+
+struct BatchPlanArgs {
+    const int64_t *off;   // [C+1] caller's offsets
+    int64_t C;
+    int64_t n_total;      // the caller's particle count (offsets[C] must equal it)
+    int64_t cap_padded;   // capacity of the padded particle array
+    int64_t cap_items;    // capacity of the item list
+    int ib;               // i-block size of the pair kernel
+    int64_t *poff;        // [C+1] padded offsets (out)
+    int2 *items;          // [cap_items] (cluster, i-block) (out)
+    int *nitems;          // item count (out)
+    int *err;             // set if the offsets do not fit the capacities
+};
+
+// Exclusive block-wide scan of one value per thread (kPlanThreads threads).
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *smem, int64_t *total) {
+    const int t = threadIdx.x;
+    smem[t] = v;
+    __syncthreads();
+    for (int d = 1; d < kPlanThreads; d <<= 1) {
+        const int64_t add = t >= d ? smem[t - d] : 0;
+        __syncthreads();
+        smem[t] += add;
+        __syncthreads();
+    }
+    const int64_t incl = smem[t];
+    *total = smem[kPlanThreads - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+__device__ __forceinline__ int size_class(int64_t psz) {
+    return psz > 0 ? 63 - __clzll((unsigned long long)psz) : -1;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPlanArgs P) {
+    __shared__ int64_t scan[kPlanThreads];
+    const int t = threadIdx.x;
+    // Offsets must start at 0, never decrease and end at n_total; otherwise
+    // every cluster is given zero size so no later kernel reads anything.
+    int bad = 0;
+    for (int64_t c = t; c < P.C; c += kPlanThreads) bad |= P.off[c + 1] < P.off[c];
+    if (t == 0) bad |= (P.off[0] != 0) | (P.off[P.C] != P.n_total);
+    const bool valid = !__syncthreads_or(bad);
+    if (!valid) {
+        for (int64_t c = t; c <= P.C; c += kPlanThreads) P.poff[c] = 0;
+        if (t == 0) {
+            *P.nitems = 0;
+            atomicOr(P.err, kErrBatchPlan);
+        }
+        return;
+    }
+    // Padded offsets.
+    int64_t carry = 0;
+    for (int64_t base = 0; base < P.C; base += kPlanThreads) {
+        const int64_t c = base + t;
+        int64_t psz = 0;
+        if (c < P.C) {
+            const int64_t nc = P.off[c + 1] - P.off[c];
+            psz = nc > 0 ? (nc + kClusterPad - 1) / kClusterPad * kClusterPad : 0;
+        }
+        int64_t total;
+        const int64_t ex = block_exclusive_scan(psz, scan, &total);
+        if (c < P.C) P.poff[c] = carry + ex;
+        carry += total;
+    }
+    if (t == 0) P.poff[P.C] = carry;
+    const bool fits = carry <= P.cap_padded;
+    // Items, largest size class first; clusters in index order within a class.
+    int64_t nit = 0;
+    for (int cls = 62; cls >= 0 && fits; --cls) {
+        for (int64_t base = 0; base < P.C; base += kPlanThreads) {
+            const int64_t c = base + t;
+            int64_t cnt = 0;
+            if (c < P.C) {
+                const int64_t nc = P.off[c + 1] - P.off[c];
+                const int64_t psz = nc > 0 ? (nc + kClusterPad - 1) / kClusterPad * kClusterPad : 0;
+                if (size_class(psz) == cls) cnt = psz / P.ib;
+            }
+            int64_t total;
+            const int64_t ex = block_exclusive_scan(cnt, scan, &total);
+            if (nit + total <= P.cap_items)
+                for (int64_t k = 0; k < cnt; ++k) P.items[nit + ex + k] = make_int2((int)c, (int)k);
+            nit += total;
+        }
+    }
+    if (t == 0) {
+        const bool ok = fits && nit <= P.cap_items;
+        *P.nitems = ok ? (int)nit : 0;
+        if (!ok) atomicOr(P.err, kErrBatchPlan);
+    }
+}
+
+// Pack cluster blockIdx.x (FP32 or FP64 source) into its padded slot.
+template <typename T>
+__global__ void batch_pack_kernel(const T *__restrict__ x, const float *__restrict__ m,
+                                  const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
+                                  JPart *__restrict__ jp) {
+    const int64_t c = blockIdx.x;
+    const int64_t o = off[c], nc = off[c + 1] - o, po = poff[c], psz = poff[c + 1] - po;
+    for (int64_t li = threadIdx.x; li < psz; li += blockDim.x) {
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+        if (li < nc) {
+            const int64_t i = o + li;
+            const float px = (float)x[3 * i], py = (float)x[3 * i + 1], pz = (float)x[3 * i + 2];
+            const float hm = -0.5f * m[i];
+            lo = make_float4(-px, -px, -py, -py);
+            hi = make_float4(-pz, -pz, hm, hm);
+        }
+        float4 *dst = reinterpret_cast<float4 *>(jp + po + li);
+        dst[0] = lo;
+        dst[1] = hi;
+    }
+}
+
+struct BatchArgs {
+    const JPart *jp;
+    const int64_t *off;
+    const int64_t *poff;
+    const float *eps;
+    const int2 *items;
+    const int *nitems;
+    int *counter;
+    float *a;
+    float *p;
+    int *err;
+    uint64_t wait_ns;
+};
+
+struct StageMeta {
+    int item, cluster, iblock, jt, end;
+};
+
+template <int THREADS, int IPT, int JT, int STAGES, bool COMP>
+__global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A) {
+    constexpr int P = IPT / 2;
+    constexpr int IB = THREADS * IPT;
+    constexpr uint32_t TILE_BYTES = JT * sizeof(JPart);
+    static_assert(kClusterPad % IB == 0 && kClusterPad % JT == 0, "tiles must divide the padding");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    JPart *tiles = reinterpret_cast<JPart *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES);
+    StageMeta *meta = reinterpret_cast<StageMeta *>(full + STAGES);
+    int *issued_at = reinterpret_cast<int *>(meta + STAGES);  // last unit copied into each stage
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            issued_at[s] = -1;
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // Producer (thread 0): walks the (item, j-tile) stream, popping items.
+    int p_item = -1, p_cluster = 0, p_b = 0, p_jt = 0, p_ntiles = 0, p_done = 0;
+    int64_t p_base = 0;
+    const int nitems = *A.nitems;
+    auto produce = [&](int kk) {
+        const int s = kk % STAGES;
+        if (!p_done && p_jt >= p_ntiles) {
+            const int it = atomicAdd(A.counter, 1);
+            if (it >= nitems) {
+                p_done = 1;
+            } else {
+                const int2 w = A.items[it];
+                p_item = it;
+                p_cluster = w.x;
+                p_b = w.y;
+                p_jt = 0;
+                p_base = A.poff[w.x];
+                p_ntiles = (int)((A.poff[w.x + 1] - p_base) / JT);
+            }
+        }
+        StageMeta mt;
+        mt.end = p_done;
+        mt.item = p_item;
+        mt.cluster = p_cluster;
+        mt.iblock = p_b;
+        mt.jt = p_jt;
+        meta[s] = mt;
+        if (p_done) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s]))
+                         : "memory");
+        } else {
+            issued_at[s] = kk;
+            mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+            bulk_g2s(tiles + (size_t)s * JT, A.jp + p_base + (int64_t)p_jt * JT, TILE_BYTES, &full[s]);
+            ++p_jt;
+        }
+    };
+    if (tid == 0)
+        for (int kk = 0; kk < STAGES - 1; ++kk) produce(kk);
+
+    float2 xi[P], yi[P], zi[P];
+    float2 sum[P][4], cmp[P][4];
+    const float2 zero2 = splat2(0.f);
+    int cur_item = -1, cur_cluster = 0, cur_b = 0;
+    float2 eps2 = zero2;
+
+    auto write_out = [&]() {
+        const int64_t o = A.off[cur_cluster], nc = A.off[cur_cluster + 1] - o;
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t li = (int64_t)cur_b * IB + (2 * q + h) * THREADS + tid;
+                if (li >= nc) continue;
+                float v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float sv = h ? sum[q][r].y : sum[q][r].x;
+                    const float cv = h ? cmp[q][r].y : cmp[q][r].x;
+                    v[r] = COMP ? __fsub_rn(sv, cv) : sv;
+                }
+                const int64_t gi = o + li;
+                A.a[3 * gi + 0] = 0.25f * v[0];
+                A.a[3 * gi + 1] = 0.25f * v[1];
+                A.a[3 * gi + 2] = 0.25f * v[2];
+                A.p[gi] = v[3];
+            }
+    };
+
+    int bad = 0;
+    int k = 0;
+    for (;; ++k) {
+        if (__syncthreads_or(bad)) break;
+        if (tid == 0) produce(k + STAGES - 1);
+        const int s = k % STAGES;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((k / STAGES) & 1), A.wait_ns)) {
+            bad = 1;
+            continue;
+        }
+        const StageMeta mt = meta[s];
+        if (mt.end) break;
+        if (mt.item != cur_item) {
+            if (cur_item >= 0) write_out();
+            cur_item = mt.item;
+            cur_cluster = mt.cluster;
+            cur_b = mt.iblock;
+            eps2 = splat2(A.eps[cur_cluster] * A.eps[cur_cluster]);
+            const int64_t base = A.poff[cur_cluster] + (int64_t)cur_b * IB;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int64_t i0 = base + (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+                const float4 A0 = reinterpret_cast<const float4 *>(A.jp + i0)[0];
+                const float4 B0 = reinterpret_cast<const float4 *>(A.jp + i0)[1];
+                const float4 A1 = reinterpret_cast<const float4 *>(A.jp + i1)[0];
+                const float4 B1 = reinterpret_cast<const float4 *>(A.jp + i1)[1];
+                xi[q] = make_float2(-A0.x, -A1.x);
+                yi[q] = make_float2(-A0.z, -A1.z);
+                zi[q] = make_float2(-B0.x, -B1.x);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    sum[q][r] = zero2;
+                    cmp[q][r] = zero2;
+                }
+            }
+        }
+        const JPart *T = tiles + (size_t)s * JT;
+        float2 acc[P][4];
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
+        const int ibase = cur_b * IB, jbase = mt.jt * JT;
+        int self0[P], self1[P];
+        if (jbase < ibase + IB && ibase < jbase + JT) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                self0[q] = ibase + (2 * q) * THREADS + tid - jbase;
+                self1[q] = self0[q] + THREADS;
+            }
+            tile_pass<P, JT, 1, true, kMixAll>(T, xi, yi, zi, acc, eps2, self0, self1);
+        } else {
+            tile_pass<P, JT, 4, false, kMixAll>(T, xi, yi, zi, acc, eps2, self0, self1);
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (COMP) {
+                    const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
+                    const float2 t = add2(sum[q][r], y);
+                    cmp[q][r] = add2(add2(t, neg2(sum[q][r])), neg2(y));
+                    sum[q][r] = t;
+                } else {
+                    sum[q][r] = add2(sum[q][r], acc[q][r]);
+                }
+            }
+    }
+    bad = __syncthreads_or(bad);
+    if (!bad) {
+        if (cur_item >= 0) write_out();
+        return;
+    }
+    if (tid == 0) {
+        atomicOr(A.err, kErrTimeout);
+        for (int s = 0; s < STAGES; ++s)
+            if (issued_at[s] >= 0)
+                mbar_wait_bounded(&full[s], (uint32_t)((issued_at[s] / STAGES) & 1), A.wait_ns);
+    }
+}
+
+// Leap-frog pieces that do not pack (the batched pack follows them).
+__global__ void batch_kick_drift_kernel(double *__restrict__ x, double *__restrict__ v,
+                                        const float *__restrict__ a, int64_t n, double dt,
+                                        int kick_back) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const double h = 0.5 * dt, g = -(double)a[k];
+    double vc = v[k];
+    if (kick_back) vc = vc + h * g;  // Eq. (3) of the previous step
+    vc = vc + h * g;                 // Eq. (1)
+    v[k] = vc;
+    x[k] = x[k] + dt * vc;           // Eq. (2)
+}
+
+__global__ void batch_kick_kernel(double *__restrict__ v, const float *__restrict__ a, int64_t n,
+                                  double dt) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    v[k] = v[k] + (0.5 * dt) * (-(double)a[k]);  // Eq. (3)
+}
+
+// Registry of batched shapes.
+template <int T, int I, int J, int S, bool C>
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t st) {
+    batched_pair_kernel<T, I, J, S, C><<<grid, T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+struct BatchVariant {
+    int threads, ipt, jtile, stages;
+    bool comp;
+    const void *kernel;
+    size_t smem;
+    cudaError_t (*launch)(const BatchArgs &, int, size_t, cudaStream_t);
+};
+
+template <int S, int J>
+constexpr size_t batch_smem() {
+    return (size_t)S * J * sizeof(JPart) + (size_t)S * sizeof(uint64_t) + S * sizeof(StageMeta) +
+           S * sizeof(int);
+}
+
+#define NB_BVARIANT(T, I, J, S, C) \
+    {T, I, J, S, C, (const void *)batched_pair_kernel<T, I, J, S, C>, batch_smem<S, J>(), launch_batched<T, I, J, S, C>}
+
+static const BatchVariant kBatch[] = {
+    NB_BVARIANT(64, 2, 128, 4, false),
+    NB_BVARIANT(64, 2, 128, 4, true),
+};
+#undef NB_BVARIANT
+
+}  // namespace nbk
+
+using namespace nbk;
+using namespace nbx;
+
+namespace {
+
+enum BSlot { B_JP = 5, B_POFF = 6, B_ITEMS = 7, B_NITEMS = 8 };
+
+void *bslot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
+
+nb_status bensure(nb_ctx *ctx, int k, size_t bytes) {
+    ExtState &s = ctx_ext(ctx);
+    cudaError_t e = ensure_buffer(&s.buf[k], &s.cap[k], bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (batched)");
+    return NB_OK;
+}
+
+struct BatchPlanHost {
+    const BatchVariant *v;
+    int64_t n_total;
+    int64_t cap_padded, cap_items;
+    int grid;
+};
+
+int batch_resident(const BatchVariant &v, int sm_count) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.kernel, v.threads, v.smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    cudaGetLastError();
+    return per_sm * sm_count;
+}
+
+// Scratch for a batch, sized from (n_total, C) alone (offsets stay on the device).
+nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, BatchPlanHost *out) {
+    const BatchVariant &v = kBatch[comp ? 1 : 0];
+    const int ib = v.threads * v.ipt;
+    out->v = &v;
+    out->n_total = n_total;
+    out->cap_padded = n_total + C * (int64_t)kClusterPad;
+    out->cap_items = out->cap_padded / ib + 1;
+    if (out->cap_items > 0x7fffffff || C > 0x7fffffff)
+        return fail(ctx, NB_ERR_ARG, "batch too large for 32-bit work items");
+    out->grid = batch_resident(v, ctx_sm_count(ctx));
+    nb_status st;
+    if ((st = bensure(ctx, B_JP, (size_t)out->cap_padded * sizeof(JPart))) != NB_OK) return st;
+    if ((st = bensure(ctx, B_POFF, (size_t)(C + 1) * sizeof(int64_t))) != NB_OK) return st;
+    if ((st = bensure(ctx, B_ITEMS, (size_t)out->cap_items * sizeof(int2))) != NB_OK) return st;
+    if ((st = bensure(ctx, B_NITEMS, 2 * sizeof(int))) != NB_OK) return st;  // count, queue head
+    return NB_OK;
+}
+
+nb_status batch_plan(nb_ctx *ctx, const int64_t *offsets, int64_t C, const BatchPlanHost &h,
+                     cudaStream_t st) {
+    BatchPlanArgs P{};
+    P.off = offsets;
+    P.C = C;
+    P.n_total = h.n_total;
+    P.cap_padded = h.cap_padded;
+    P.cap_items = h.cap_items;
+    P.ib = h.v->threads * h.v->ipt;
+    P.poff = static_cast<int64_t *>(bslot(ctx, B_POFF));
+    P.items = static_cast<int2 *>(bslot(ctx, B_ITEMS));
+    P.nitems = static_cast<int *>(bslot(ctx, B_NITEMS));
+    P.err = ctx_err_word(ctx);
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch plan launch");
+    return NB_OK;
+}
+
+// pack (already done by the caller of this helper) -> reset queue -> pair kernel
+nb_status batch_pair(nb_ctx *ctx, const int64_t *offsets, int64_t C, const float *eps, float *a,
+                     float *p, const BatchPlanHost &h, cudaStream_t st) {
+    int *nit = static_cast<int *>(bslot(ctx, B_NITEMS));
+    cudaError_t e = cudaMemsetAsync(nit + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "queue reset");
+    BatchArgs A{};
+    A.jp = static_cast<const JPart *>(bslot(ctx, B_JP));
+    A.off = offsets;
+    A.poff = static_cast<const int64_t *>(bslot(ctx, B_POFF));
+    A.eps = eps;
+    A.items = static_cast<const int2 *>(bslot(ctx, B_ITEMS));
+    A.nitems = nit;
+    A.counter = nit + 1;
+    A.a = a;
+    A.p = p;
+    A.err = ctx_err_word(ctx);
+    A.wait_ns = ctx_wait_ns(ctx);
+    {
+        TimedLaunch t(ctx, 4, st);
+        e = h.v->launch(A, h.grid, h.v->smem, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched pair kernel launch");
+    return NB_OK;
+}
+
+nb_status check_batch_args(nb_ctx *ctx, int64_t C, int64_t n_total, int mode) {
+    if (C < 0 || n_total < 0) return fail(ctx, NB_ERR_ARG, "n_clusters and n_total must be >= 0");
+    if (mode != NB_PLAIN && mode != NB_COMPENSATED) return fail(ctx, NB_ERR_ARG, "unknown mode");
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const int64_t *offsets,
+                           int64_t n_clusters, int64_t n_total, const float *eps, float *a, float *p,
+                           nb_mode mode, void *stream) {
+    if (!ctx) return NB_ERR_ARG;
+    nb_status st = check_batch_args(ctx, n_clusters, n_total, mode);
+    if (st != NB_OK) return st;
+    if (n_clusters == 0 || n_total == 0) return NB_OK;
+    if (!x || !m || !offsets || !eps || !a || !p) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    DeviceGuard g(ctx_device(ctx));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchPlanHost h{};
+    if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
+    if ((st = batch_plan(ctx, offsets, n_clusters, h, s)) != NB_OK) return st;
+    batch_pack_kernel<float><<<(unsigned)n_clusters, 256, 0, s>>>(
+        x, m, offsets, static_cast<const int64_t *>(bslot(ctx, B_POFF)),
+        static_cast<JPart *>(bslot(ctx, B_JP)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched pack launch");
+    return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);
+}
+
+nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const float *m,
+                                   const int64_t *offsets, int64_t n_clusters, int64_t n_total,
+                                   const float *eps, float *a, float *p, double dt, int nsteps,
+                                   int a_valid, nb_mode mode, void *stream) {
+    if (!ctx) return NB_ERR_ARG;
+    nb_status st = check_batch_args(ctx, n_clusters, n_total, mode);
+    if (st != NB_OK) return st;
+    if (nsteps < 0) return fail(ctx, NB_ERR_ARG, "nsteps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ctx, NB_ERR_ARG, "dt must be finite");
+    if (n_clusters == 0 || n_total == 0) return NB_OK;
+    if (!x || !v || !m || !offsets || !eps || !a || !p)
+        return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    DeviceGuard g(ctx_device(ctx));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchPlanHost h{};
+    if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
+    if ((st = batch_plan(ctx, offsets, n_clusters, h, s)) != NB_OK) return st;
+    const int64_t *poff = static_cast<const int64_t *>(bslot(ctx, B_POFF));
+    JPart *jp = static_cast<JPart *>(bslot(ctx, B_JP));
+    const unsigned nb3 = (unsigned)((3 * n_total + 255) / 256);
+    cudaError_t e;
+
+    auto force = [&]() -> nb_status {
+        batch_pack_kernel<double><<<(unsigned)n_clusters, 256, 0, s>>>(x, m, offsets, poff, jp);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "batched pack launch");
+        return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);
+    };
+    auto step = [&](int kick_back) -> nb_status {
+        batch_kick_drift_kernel<<<nb3, 256, 0, s>>>(x, v, a, n_total, dt, kick_back);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "leap-frog update launch");
+        return force();
+    };
+
+    if (!a_valid && (st = force()) != NB_OK) return st;
+    if (nsteps == 0) return NB_OK;
+    if ((st = step(0)) != NB_OK) return st;
+    const int rest = nsteps - 1;
+    if (rest >= 2 && s != nullptr) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
+        const bool timing = ctx_set_timing(ctx, false);
+        nb_status cst = step(1);
+        ctx_set_timing(ctx, timing);
+        e = cudaStreamEndCapture(s, &graph);
+        if (cst != NB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cst;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+        for (int k = 0; k < rest && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    } else {
+        for (int k = 0; k < rest; ++k)
+            if ((st = step(1)) != NB_OK) return st;
+    }
+    batch_kick_kernel<<<nb3, 256, 0, s>>>(v, a, n_total, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "kick launch");
+    return NB_OK;
+}
+
+}  // extern "C"

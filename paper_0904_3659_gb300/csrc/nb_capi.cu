@@ -392,6 +392,10 @@ nb_status nb_synchronize(nb_ctx *ctx, void *stream) {
         if (word & nbdev::kErrTimeout)
             return fail(ctx, NB_ERR_TIMEOUT,
                         "a bounded wait for a shared-memory tile ran out; results are invalid");
+        if (word & nbdev::kErrBatchPlan)
+            return fail(ctx, NB_ERR_ARG,
+                        "batched offsets are invalid (they must start at 0, never decrease and "
+                        "end at n_total); nothing was computed");
         return fail(ctx, NB_ERR_CUDA, "device error word set");
     }
     return NB_OK;

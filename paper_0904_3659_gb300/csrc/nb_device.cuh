@@ -10,6 +10,7 @@ namespace nbdev {
 
 // Error bits a kernel records in the context's device error word.
 constexpr int kErrTimeout = 1;
+constexpr int kErrBatchPlan = 2;  // batched offsets exceed the capacity sized from n_total
 
 // Default limit for one bounded wait on a shared-memory barrier.
 constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // one second

@@ -33,6 +33,7 @@
 
 #include "nb_device.cuh"
 #include "nb_internal.h"
+#include "nb_tile.cuh"
 
 namespace nbk {
 using namespace nbdev;
@@ -54,80 +55,6 @@ __global__ void pack_f32_kernel(const float *__restrict__ x, const float *__rest
     float4 *dst = reinterpret_cast<float4 *>(jp + i);
     dst[0] = lo;
     dst[1] = hi;
-}
-
-// ---------------------------------------------------------------------------
-// One pass of a j-tile against the thread's P pairs of i-particles.
-// acc[q][0..2] += 4 m_j y1^3 (x_i - x_j), acc[q][3] += m_j y1, where
-// y1 = y (3 - s y^2) / 2 is one Newton-Raphson step for f(y) = y^-2 - s from
-// the special-function unit's estimate y of s^{-1/2}. With t = s y^2 - 3 and
-// u = y t we have y1 = -u/2, so m_j y1 = (-m_j/2) u (the packed mass is
-// stored as -m_j/2) and 4 m_j y1^3 = (m_j y1) u^2.
-// In a diagonal tile (DIAG) the j == i term is removed by zeroing the mass
-// lane of the thread's own particle; self0/self1 give, per pair, the tile
-// position of the thread's own i (outside [0, JT) when it is not here).
-// Operation groups of one interaction. Bit g of a MIX mask set: the group
-// runs as packed FP32x2 instructions; clear: as two scalar FP32 instructions
-// (same IEEE round-to-nearest operations, so every mask gives bit-identical
-// results). Mixing trades issue slots (packed: one per two lanes) against
-// the lower sustained pipe rate of packed instructions.
-enum : int { kMixD = 1, kMixS = 2, kMixN = 4, kMixQ = 8, kMixW = 16, kMixA = 32, kMixAll = 63 };
-
-template <bool PK>
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) {
-    return PK ? add2(a, b) : make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
-}
-template <bool PK>
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) {
-    return PK ? mul2(a, b) : make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
-}
-template <bool PK>
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
-    return PK ? fma2(a, b, c) : make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
-}
-
-template <int P, int JT, int UNR, bool DIAG, int MIX>
-__device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const float2 (&xi)[P],
-                                          const float2 (&yi)[P], const float2 (&zi)[P],
-                                          float2 (&acc)[P][4], const float2 eps2,
-                                          const int (&self0)[P], const int (&self1)[P]) {
-    const float2 m3 = splat2(-3.f);
-#pragma unroll UNR
-    for (int jj = 0; jj < JT; ++jj) {
-        const float4 A = reinterpret_cast<const float4 *>(T + jj)[0];
-        const float4 B = reinterpret_cast<const float4 *>(T + jj)[1];
-        const float2 nxj = make_float2(A.x, A.y);
-        const float2 nyj = make_float2(A.z, A.w);
-        const float2 nzj = make_float2(B.x, B.y);
-        const float2 hmj = make_float2(B.z, B.w);
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            constexpr bool PD = MIX & kMixD, PS = MIX & kMixS, PN = MIX & kMixN;
-            constexpr bool PQ = MIX & kMixQ, PW = MIX & kMixW, PA = MIX & kMixA;
-            const float2 dx = vadd<PD>(xi[q], nxj);
-            const float2 dy = vadd<PD>(yi[q], nyj);
-            const float2 dz = vadd<PD>(zi[q], nzj);
-            float2 s = vfma<PS>(dx, dx, eps2);
-            s = vfma<PS>(dy, dy, s);
-            s = vfma<PS>(dz, dz, s);
-            const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
-            const float2 y2 = vmul<PN>(y, y);
-            const float2 t = vfma<PN>(s, y2, m3);
-            const float2 u = vmul<PN>(y, t);
-            float2 hm = hmj;
-            if (DIAG) {
-                if (jj == self0[q]) hm.x = 0.f;
-                if (jj == self1[q]) hm.y = 0.f;
-            }
-            const float2 qv = vmul<PQ>(hm, u);
-            acc[q][3] = vadd<PQ>(acc[q][3], qv);
-            const float2 u2 = vmul<PW>(u, u);
-            const float2 w = vmul<PW>(qv, u2);
-            acc[q][0] = vfma<PA>(w, dx, acc[q][0]);
-            acc[q][1] = vfma<PA>(w, dy, acc[q][1]);
-            acc[q][2] = vfma<PA>(w, dz, acc[q][2]);
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------

@@ -6,12 +6,6 @@ using namespace nbx;
 
 extern "C" {
 
-nb_status nb_force_batched(nb_ctx *ctx, const float *, const float *, const int64_t *, int64_t,
-                           int64_t, const float *, float *, float *, nb_mode, void *) {
-    if (!ctx) return NB_ERR_ARG;
-    return fail(ctx, NB_ERR_NOT_IMPLEMENTED, "nb_force_batched is not built yet");
-}
-
 nb_status nb_force_vjp(nb_ctx *ctx, const float *, const float *, int64_t, float, const float *,
                        const float *, float *, float *, void *) {
     if (!ctx) return NB_ERR_ARG;
