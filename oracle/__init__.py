@@ -14,6 +14,9 @@ Functions, each following the paper (Fujiwara & Nakasato, arXiv:0904.3659):
   force_vjp    chain rule of Eq. (gravity): dL/dx, dL/dm for
                L = sum_i ga_i . a_i + gp_i p_i
   leapfrog     Eqs. (1)-(3), Section "Method", with the physical sign g = -a
+  leapfrog_grad  reverse-mode chain rule through leapfrog's steps (uses
+               force_vjp): gradients at the initial state of a loss of the
+               final state
   energy       K = 1/2 sum m v^2, W = -1/2 sum m p
 
 Parity status: every function is pinned by CPU tests against closed forms,
@@ -173,6 +176,50 @@ def leapfrog(x, v, m, eps, dt, nsteps):
         _load().nbo_leapfrog(n, _p(x), _p(v), _p(m), _eps64(eps), float(dt),
                              int(nsteps), _p(g), _p(work))
     return x, v, g
+
+
+def leapfrog_grad(x0, v0, m, eps, dt, nsteps, xbar, vbar=None):
+    """Gradients (dL/dx0, dL/dv0, dL/dm) of a loss L of the state after
+    nsteps leapfrog steps, given xbar = dL/dx(T) and vbar = dL/dv(T).
+
+    Chain rule through the steps of `leapfrog` in reverse. One step maps
+    (x, v, a) with a = Eq. (gravity) at x to
+        x' = x + dt v - dt^2/2 a          Eq. (2) with g = -a
+        a' = Eq. (gravity) at x'
+        v' = v - dt/2 a - dt/2 a'         Eqs. (1) and (3)
+    so, going back, the adjoint of a' collects -dt/2 vbar', the adjoint of
+    x' collects the VJP of Eq. (gravity) at x' (force_vjp, which also gives
+    the mass gradient), the adjoint of a collects -dt/2 vbar' - dt^2/2 xbar',
+    and vbar = vbar' + dt xbar', xbar = xbar'.
+    """
+    x = _f64(x0).copy()
+    n = x.shape[0]
+    x = x.reshape(n, 3)
+    v = _f64(v0, (n, 3)).copy()
+    m = _f64(m, (n,))
+    eps = _eps64(eps)
+    xs = [x.copy()]
+    a, _, _ = force(x, m, eps)
+    for _ in range(int(nsteps)):
+        v_half = v + 0.5 * dt * (-a)
+        x = x + v * dt + 0.5 * (-a) * dt * dt
+        a, _, _ = force(x, m, eps)
+        v = v_half + 0.5 * dt * (-a)
+        xs.append(x.copy())
+    xb = _f64(xbar, (n, 3)).copy()
+    vb = np.zeros((n, 3)) if vbar is None else _f64(vbar, (n, 3)).copy()
+    ab = np.zeros((n, 3))
+    mb = np.zeros(n)
+    zero_p = np.zeros(n)
+    for s in range(int(nsteps) - 1, -1, -1):
+        ab_next = ab - 0.5 * dt * vb
+        gx, gm = force_vjp(xs[s + 1], m, eps, ab_next, zero_p)
+        xb = xb + gx
+        mb = mb + gm
+        ab = -0.5 * dt * vb - 0.5 * dt * dt * xb
+        vb = vb + dt * xb
+    gx, gm = force_vjp(xs[0], m, eps, ab, zero_p)
+    return xb + gx, vb, mb + gm
 
 
 def energy(x, v, m, eps):

@@ -1,0 +1,356 @@
+// nb_vjp.cu -- vector-Jacobian product of Eq. (gravity) (Fujiwara & Nakasato,
+// arXiv:0904.3659, Section "Introduction"): for upstream gradients ga_i (on
+// a_i) and gp_i (on p_i), the gradient of L = sum_i ga_i . a_i + gp_i p_i
+// with respect to positions and masses, as one gather pass over all pairs.
+//
+// For particle i and every l != i, with r = x_i - x_l, s = |r|^2 + eps^2 and
+// y = s^{-1/2} (chain rule of the definition):
+//   gx_i += m_l [y^3 ga_i - 3 y^5 (r.ga_i) r - gp_i y^3 r]
+//         - m_i [y^3 ga_l - 3 y^5 (r.ga_l) r + gp_l y^3 r]
+//   gm_i += -(r.ga_l) y^3 + gp_l y
+// Regrouped per pair into a coefficient of r and three sums:
+//   gx_i = ga_i sum_l m_l y^3 - m_i sum_l y^3 ga_l + sum_l c_il r
+//   c_il = 3 y^5 (m_i r.ga_l - m_l r.ga_i) - y^3 (gp_i m_l + m_i gp_l)
+// With the Newton-refined y1 = -u/2 (u as in the force kernel): y^3 = -u^3/8,
+// y^5 = -u^5/32, so
+//   32 c_il = u^5 (m_l (3 ga_i).r + (-3 m_i) ga_l.r) + u^3 (4 gp_i m_l + (-m_i)(-4 gp_l))
+// The kernel accumulates, per i,
+//   R = sum 32 c_il r,  S = sum m_l u^3,  V = sum u^3 ga_l,
+//   G = sum ((r.ga_l) u^3 + (-4 gp_l) u)
+// and the combine forms gx_i = R/32 - ga_i S/8 + m_i V/8, gm_i = G/8
+// (the 1/8 and 1/32 are exact scalings). 33 FP32 operations and one
+// special-function reciprocal square root per pair.
+#include <algorithm>
+#include <cmath>
+
+#include "nb_device.cuh"
+#include "nb_ext.h"
+#include "nb_internal.h"
+
+namespace nbk {
+using namespace nbdev;
+
+// One j-particle of the VJP pass, 64 bytes, each value duplicated for packed
+// FP32x2 use: (-x, -y, -z, m, ga_x, ga_y, ga_z, -4 gp).
+struct alignas(64) VPart {
+    float2 nx, ny, nz, m, gx, gy, gz, gp4n;
+};
+static_assert(sizeof(VPart) == 64, "VPart must be 64 bytes");
+
+__global__ void vjp_pack_kernel(const float *__restrict__ x, const float *__restrict__ m,
+                                const float *__restrict__ ga, const float *__restrict__ gp,
+                                int64_t n, int64_t npad, VPart *__restrict__ vp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < n) {
+        v[0] = -x[3 * i];
+        v[1] = -x[3 * i + 1];
+        v[2] = -x[3 * i + 2];
+        v[3] = m[i];
+        v[4] = ga[3 * i];
+        v[5] = ga[3 * i + 1];
+        v[6] = ga[3 * i + 2];
+        v[7] = -4.f * gp[i];
+    }
+    float4 *dst = reinterpret_cast<float4 *>(vp + i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = make_float4(v[2 * k], v[2 * k], v[2 * k + 1], v[2 * k + 1]);
+}
+
+struct VjpArgs {
+    const VPart *vp;
+    const float *x, *m, *ga, *gp;  // originals (i-side constants)
+    float4 *partial;               // [grid][maxseg][2][ib]
+    int *err;
+    int64_t n, njt, units;
+    int grid, maxseg;
+    float eps2;
+    uint64_t wait_ns;
+};
+
+template <int P, int JT, int UNR, bool DIAG>
+__device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const float2 (&xi)[P],
+                                         const float2 (&yi)[P], const float2 (&zi)[P],
+                                         const float2 (&g3x)[P], const float2 (&g3y)[P],
+                                         const float2 (&g3z)[P], const float2 (&nm3)[P],
+                                         const float2 (&gp4)[P], const float2 (&nm)[P],
+                                         float2 (&acc)[P][8], const float2 eps2,
+                                         const int (&self0)[P], const int (&self1)[P]) {
+    const float2 m3 = splat2(-3.f);
+#pragma unroll UNR
+    for (int jj = 0; jj < JT; ++jj) {
+        const float4 A = reinterpret_cast<const float4 *>(T + jj)[0];
+        const float4 B = reinterpret_cast<const float4 *>(T + jj)[1];
+        const float4 C = reinterpret_cast<const float4 *>(T + jj)[2];
+        const float4 D = reinterpret_cast<const float4 *>(T + jj)[3];
+        const float2 nxj = make_float2(A.x, A.y), nyj = make_float2(A.z, A.w);
+        const float2 nzj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+        const float2 gxj = make_float2(C.x, C.y), gyj = make_float2(C.z, C.w);
+        const float2 gzj = make_float2(D.x, D.y), gp4nj = make_float2(D.z, D.w);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float2 dx = add2(xi[q], nxj), dy = add2(yi[q], nyj), dz = add2(zi[q], nzj);
+            float2 s = fma2(dx, dx, eps2);
+            s = fma2(dy, dy, s);
+            s = fma2(dz, dz, s);
+            const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
+            float2 u = mul2(y, fma2(s, mul2(y, y), m3));  // u = -2 y1
+            if (DIAG) {
+                if (jj == self0[q]) u.x = 0.f;
+                if (jj == self1[q]) u.y = 0.f;
+            }
+            const float2 u2 = mul2(u, u);
+            const float2 u3 = mul2(u, u2);
+            const float2 u5 = mul2(u3, u2);
+            const float2 dgi3 = fma2(dz, g3z[q], fma2(dy, g3y[q], mul2(dx, g3x[q])));  // 3 r.ga_i
+            const float2 dgj = fma2(dz, gzj, fma2(dy, gyj, mul2(dx, gxj)));           // r.ga_l
+            const float2 a3 = fma2(mj, dgi3, mul2(nm3[q], dgj));
+            const float2 b4 = fma2(gp4[q], mj, mul2(nm[q], gp4nj));
+            const float2 c32 = fma2(u5, a3, mul2(u3, b4));
+            acc[q][0] = fma2(c32, dx, acc[q][0]);
+            acc[q][1] = fma2(c32, dy, acc[q][1]);
+            acc[q][2] = fma2(c32, dz, acc[q][2]);
+            acc[q][3] = fma2(mj, u3, acc[q][3]);
+            acc[q][4] = fma2(u3, gxj, acc[q][4]);
+            acc[q][5] = fma2(u3, gyj, acc[q][5]);
+            acc[q][6] = fma2(u3, gzj, acc[q][6]);
+            acc[q][7] = fma2(gp4nj, u, fma2(dgj, u3, acc[q][7]));
+        }
+    }
+}
+
+template <int THREADS, int IPT, int JT, int STAGES>
+__global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
+    constexpr int P = IPT / 2;
+    constexpr int IB = THREADS * IPT;
+    constexpr uint32_t TILE_BYTES = JT * sizeof(VPart);
+    static_assert(kPad % IB == 0 && kPad % JT == 0, "tile sizes must divide the padding");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    VPart *tiles = reinterpret_cast<VPart *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES);
+
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    const int64_t u0 = c * args.units / args.grid;
+    const int64_t u1 = (c + 1) * args.units / args.grid;
+    const int count = (int)(u1 - u0);
+    const int64_t bfirst = u0 / args.njt;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int issued = 0;
+    auto issue_next = [&]() {
+        const int s = issued % STAGES;
+        const int64_t jt = (u0 + issued) % args.njt;
+        mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+        bulk_g2s(tiles + (size_t)s * JT, args.vp + jt * JT, TILE_BYTES, &full[s]);
+        ++issued;
+    };
+    if (tid == 0)
+        while (issued < count && issued < STAGES - 1) issue_next();
+
+    float2 xi[P], yi[P], zi[P], g3x[P], g3y[P], g3z[P], nm3[P], gp4[P], nm[P];
+    float2 sum[P][8];
+    const float2 eps2 = splat2(args.eps2);
+    const float2 zero2 = splat2(0.f);
+
+    auto flush = [&](int64_t b) {
+        float4 *dst = args.partial + (c * args.maxseg + (b - bfirst)) * 2 * (int64_t)IB;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int i0 = (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+            dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
+            dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+            dst[IB + i0] = make_float4(sum[q][4].x, sum[q][5].x, sum[q][6].x, sum[q][7].x);
+            dst[IB + i1] = make_float4(sum[q][4].y, sum[q][5].y, sum[q][6].y, sum[q][7].y);
+        }
+    };
+
+    int64_t b = u0 / args.njt;
+    int64_t jt = u0 - b * args.njt;
+    int64_t cur_b = -1;
+    int bad = 0, k = 0;
+    for (; k < count; ++k) {
+        if (__syncthreads_or(bad)) break;
+        if (tid == 0 && issued < count) issue_next();
+        if (b != cur_b) {
+            if (cur_b >= 0) flush(cur_b);
+            cur_b = b;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                float e[2][9];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t i = b * IB + (2 * q + h) * THREADS + tid;
+                    const VPart &V = args.vp[i];
+                    e[h][0] = -V.nx.x;
+                    e[h][1] = -V.ny.x;
+                    e[h][2] = -V.nz.x;
+                    e[h][3] = 3.f * V.gx.x;
+                    e[h][4] = 3.f * V.gy.x;
+                    e[h][5] = 3.f * V.gz.x;
+                    e[h][6] = -3.f * V.m.x;
+                    e[h][7] = -V.gp4n.x;  // 4 gp_i
+                    e[h][8] = -V.m.x;
+                }
+                xi[q] = make_float2(e[0][0], e[1][0]);
+                yi[q] = make_float2(e[0][1], e[1][1]);
+                zi[q] = make_float2(e[0][2], e[1][2]);
+                g3x[q] = make_float2(e[0][3], e[1][3]);
+                g3y[q] = make_float2(e[0][4], e[1][4]);
+                g3z[q] = make_float2(e[0][5], e[1][5]);
+                nm3[q] = make_float2(e[0][6], e[1][6]);
+                gp4[q] = make_float2(e[0][7], e[1][7]);
+                nm[q] = make_float2(e[0][8], e[1][8]);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) sum[q][r] = zero2;
+            }
+        }
+        const int s = k % STAGES;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((k / STAGES) & 1), args.wait_ns)) {
+            bad = 1;
+            continue;
+        }
+        const VPart *T = tiles + (size_t)s * JT;
+        float2 acc[P][8];
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) acc[q][r] = zero2;
+        const int64_t ibase = b * IB, jbase = jt * JT;
+        int self0[P], self1[P];
+        if (jbase < ibase + IB && ibase < jbase + JT) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
+                self1[q] = self0[q] + THREADS;
+            }
+            vjp_tile<P, JT, 1, true>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0, self1);
+        } else {
+            vjp_tile<P, JT, 2, false>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
+                                   self1);
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) sum[q][r] = add2(sum[q][r], acc[q][r]);
+        if (++jt == args.njt) {
+            jt = 0;
+            ++b;
+        }
+    }
+    bad = __syncthreads_or(bad);
+    if (!bad) {
+        if (cur_b >= 0) flush(cur_b);
+        return;
+    }
+    if (tid == 0) {
+        atomicOr(args.err, kErrTimeout);
+        for (int kk = (k > 0 ? k - 1 : 0); kk < issued; ++kk)
+            mbar_wait_bounded(&full[kk % STAGES], (uint32_t)((kk / STAGES) & 1), args.wait_ns);
+    }
+}
+
+// Combine the per-segment sums of each i (CTA order) and form gx, gm.
+__global__ void vjp_combine_kernel(const VjpArgs A, int ib, float *__restrict__ gx,
+                                   float *__restrict__ gm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    const int64_t b = i / ib, w = i - b * ib;
+    const int64_t clo = ((b * A.njt + 1) * (int64_t)A.grid - 1) / A.units;
+    const int64_t chi = (((b + 1) * A.njt) * (int64_t)A.grid - 1) / A.units;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t c = clo; c <= chi; ++c) {
+        const int64_t bf = (c * A.units / A.grid) / A.njt;
+        const int64_t base = (c * A.maxseg + (b - bf)) * 2 * ib + w;
+        const float4 p0 = A.partial[base], p1 = A.partial[base + ib];
+        const float v[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+        for (int r = 0; r < 8; ++r) s[r] = __fadd_rn(s[r], v[r]);
+    }
+    const float mi = A.m[i];
+    // gx = R/32 - ga_i S/8 + m_i V/8
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float gai = A.ga[3 * i + c];
+        const float t = __fmaf_rn(mi, 0.125f * s[4 + c], -(gai * (0.125f * s[3])));
+        gx[3 * i + c] = __fadd_rn(0.03125f * s[c], t);
+    }
+    gm[i] = 0.125f * s[7];
+}
+
+}  // namespace nbk
+
+using namespace nbk;
+using namespace nbx;
+
+namespace {
+
+constexpr int kVThreads = 128, kVIpt = 4, kVJt = 128, kVStages = 3;
+enum VSlot { V_VP = 9, V_PART = 10 };
+
+}  // namespace
+
+extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
+                                  const float *ga, const float *gp, float *gx, float *gm,
+                                  void *stream) {
+    if (!ctx) return NB_ERR_ARG;
+    nb_status st = check_common(ctx, n, eps, NB_PLAIN);
+    if (st != NB_OK) return st;
+    if (n == 0) return NB_OK;
+    if (!x || !m || !ga || !gp || !gx || !gm) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    DeviceGuard g(ctx_device(ctx));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    using K = void (*)(const VjpArgs);
+    const K kernel = vjp_kernel<kVThreads, kVIpt, kVJt, kVStages>;
+    const size_t smem = (size_t)kVStages * kVJt * sizeof(VPart) + kVStages * sizeof(uint64_t);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kernel, kVThreads, smem);
+    cudaGetLastError();
+    PairVariant shape{};
+    shape.tile.threads = kVThreads;
+    shape.tile.ipt = kVIpt;
+    shape.tile.jtile = kVJt;
+    shape.comp = true;  // two float4 words per i
+    const PairPlan plan = make_plan(shape, n, std::max(per_sm, 1) * ctx_sm_count(ctx));
+
+    ExtState &es = ctx_ext(ctx);
+    cudaError_t e = ensure_buffer(&es.buf[V_VP], &es.cap[V_VP], (size_t)plan.npad * sizeof(VPart));
+    if (e == cudaSuccess)
+        e = ensure_buffer(&es.buf[V_PART], &es.cap[V_PART], plan.partial_bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (vjp)");
+    VPart *vp = static_cast<VPart *>(es.buf[V_VP]);
+    vjp_pack_kernel<<<(unsigned)((plan.npad + 255) / 256), 256, 0, s>>>(x, m, ga, gp, n, plan.npad, vp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp pack launch");
+
+    VjpArgs A{};
+    A.vp = vp;
+    A.x = x;
+    A.m = m;
+    A.ga = ga;
+    A.gp = gp;
+    A.partial = static_cast<float4 *>(es.buf[V_PART]);
+    A.err = ctx_err_word(ctx);
+    A.n = n;
+    A.njt = plan.njt;
+    A.units = plan.units;
+    A.grid = plan.grid;
+    A.maxseg = plan.maxseg;
+    A.eps2 = eps * eps;
+    A.wait_ns = ctx_wait_ns(ctx);
+    {
+        TimedLaunch t(ctx, 5, s);
+        kernel<<<plan.grid, kVThreads, smem, s>>>(A);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp kernel launch");
+    vjp_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, plan.ib, gx, gm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp combine launch");
+    return NB_OK;
+}

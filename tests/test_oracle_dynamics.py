@@ -188,3 +188,36 @@ def test_leapfrog_circular_two_body(oracle_mod):
     sep = np.linalg.norm(x1[0] - x1[1])
     assert sep == pytest.approx(1.0, abs=1e-5)
     np.testing.assert_allclose(x1, x, atol=2e-4)
+
+
+def test_leapfrog_grad_matches_central_differences(oracle_mod):
+    # The reverse-mode trajectory gradient against central differences of the
+    # forward integrator, for every coordinate of x0, v0 and m.
+    n, eps, dt, steps = 12, float(np.float32(0.1)), 0.02, 10
+    x0, v0, m = workloads.plummer(n, seed=41)
+    y = workloads.targets(x0, seed=42)
+
+    def L(xx, vv, mm):
+        xT, vT, _ = oracle_mod.leapfrog(xx, vv, mm, eps, dt, steps)
+        return float(((xT - y) ** 2).sum() + 0.5 * (vT ** 2).sum())
+
+    xT, vT, _ = oracle_mod.leapfrog(x0, v0, m, eps, dt, steps)
+    gx, gv, gm = oracle_mod.leapfrog_grad(x0, v0, m, eps, dt, steps, 2 * (xT - y), vT)
+    for arr, grad, hs in ((x0, gx, 1e-5), (v0, gv, 1e-5)):
+        for i in range(n):
+            for c in range(3):
+                p_, q_ = arr.copy(), arr.copy()
+                p_[i, c] += hs
+                q_[i, c] -= hs
+                if arr is x0:
+                    fd = (L(p_, v0, m) - L(q_, v0, m)) / (2 * hs)
+                else:
+                    fd = (L(x0, p_, m) - L(x0, q_, m)) / (2 * hs)
+                assert grad[i, c] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    for i in range(n):
+        h = 1e-3 * m[i]
+        p_, q_ = m.copy(), m.copy()
+        p_[i] += h
+        q_[i] -= h
+        fd = (L(x0, v0, p_) - L(x0, v0, q_)) / (2 * h)
+        assert gm[i] == pytest.approx(fd, rel=1e-6, abs=1e-8)

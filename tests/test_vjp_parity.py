@@ -1,0 +1,255 @@
+"""GPU checks of the adjoint: nb_force_vjp against the oracle's VJP, the
+autograd Function, and gradients of a leap-frog trajectory loss (Section
+"Method", Eqs. (1)-(3)) against FP64 finite differences of the oracle's
+trajectory.
+
+VJP error measure: per particle, |g_gpu - g_ref| divided by the sum of the
+magnitudes of that particle's terms (the analogue of A_i for the force; the
+sums cancel strongly, so |g_ref| itself is no scale); tolerance 1e-5.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0904_3659_gb300 import build
+    build.build()
+    import paper_0904_3659_gb300 as nbmod
+    return nbmod
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    c = nb.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_vjp(nb, ctx, x32, m32, eps, ga, gp):
+    import torch
+    dev = torch.device("cuda:0")
+    n = x32.shape[0]
+    t = lambda arr: torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float32)).to(dev)
+    gx = torch.full((n, 3), float("nan"), device=dev)
+    gm = torch.full((n,), float("nan"), device=dev)
+    nb.nb_force_vjp(ctx, t(x32), t(m32), n, eps, t(ga), t(gp), gx, gm)
+    nb.nb_synchronize(ctx)
+    return gx.cpu().numpy(), gm.cpu().numpy()
+
+
+def vjp_term_scales(x, m, eps, ga, gp, chunk=512):
+    """Per particle k, the sums over l != k of the magnitudes of the terms of
+    gx_k and gm_k (r = x_k - x_l, s = |r|^2 + eps^2, y = s^-1/2):
+      Gx_k = sum m_l (y^3 |ga_k| + 3 y^5 |r.ga_k| |r| + |gp_k| y^3 |r|)
+           + m_k (y^3 |ga_l| + 3 y^5 |r.ga_l| |r| + |gp_l| y^3 |r|)
+      Gm_k = sum |r.ga_l| y^3 + |gp_l| y"""
+    x = np.asarray(x, np.float64)
+    m = np.asarray(m, np.float64)
+    ga = np.asarray(ga, np.float64)
+    gp = np.asarray(gp, np.float64)
+    n = x.shape[0]
+    e2 = float(np.float32(eps)) ** 2
+    gx_s = np.zeros(n)
+    gm_s = np.zeros(n)
+    nga = np.linalg.norm(ga, axis=1)
+    for k0 in range(0, n, chunk):
+        k1 = min(n, k0 + chunk)
+        r = x[k0:k1, None, :] - x[None, :, :]
+        r2 = (r * r).sum(-1)
+        y = 1.0 / np.sqrt(r2 + e2)
+        idx = np.arange(k0, k1)
+        y[idx - k0, idx] = 0.0                       # j != i
+        y3, y5, rn = y ** 3, y ** 5, np.sqrt(r2)
+        rgk = np.abs((r * ga[k0:k1, None, :]).sum(-1))
+        rgl = np.abs((r * ga[None, :, :]).sum(-1))
+        gx_s[k0:k1] = (m[None, :] * (y3 * nga[k0:k1, None] + 3 * y5 * rgk * rn
+                                     + np.abs(gp[k0:k1, None]) * y3 * rn)).sum(1)
+        gx_s[k0:k1] += m[k0:k1] * (y3 * nga[None, :] + 3 * y5 * rgl * rn
+                                   + np.abs(gp[None, :]) * y3 * rn).sum(1)
+        gm_s[k0:k1] = (rgl * y3 + np.abs(gp[None, :]) * y).sum(1)
+    return gx_s, gm_s
+
+
+def rel_to_scale(g, ref, scale):
+    d = np.linalg.norm(np.atleast_2d((np.asarray(g, np.float64) - ref).T).T, axis=-1)
+    return float(np.max(d / scale))
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 700, 3001, 8192])
+def test_vjp_matches_oracle(nb, ctx, oracle_mod, n):
+    x, _, m = workloads.plummer(n, seed=n)
+    x32, m32 = x.astype(np.float32), m.astype(np.float32)
+    rng = np.random.default_rng(n + 1)
+    ga = rng.normal(size=(n, 3)).astype(np.float32)
+    gp = rng.normal(size=n).astype(np.float32)
+    eps = np.float32(1.0 / 64)
+    gx, gm = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
+    rgx, rgm = oracle_mod.force_vjp(x32, m32, eps, ga, gp)
+    assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gm))
+    if n == 1:
+        assert np.all(gx == 0) and np.all(gm == 0)
+        return
+    sx, sm = vjp_term_scales(x32, m32, eps, ga, gp)
+    assert rel_to_scale(gx, rgx, sx) <= 1e-5
+    assert rel_to_scale(gm, rgm, sm) <= 1e-5
+
+
+def test_vjp_repeatable_and_dot_product(nb, ctx, oracle_mod):
+    # Bit-reproducible; and <J dtheta, w> = <dtheta, J^T w> with J dtheta from
+    # a central FP64 difference of the oracle's forward.
+    n = 2000
+    x, _, m = workloads.plummer(n, seed=9)
+    x32, m32 = x.astype(np.float32), m.astype(np.float32)
+    rng = np.random.default_rng(10)
+    ga = rng.normal(size=(n, 3)).astype(np.float32)
+    gp = rng.normal(size=n).astype(np.float32)
+    eps = np.float32(0.02)
+    gx, gm = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
+    gx2, gm2 = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
+    assert gx.tobytes() == gx2.tobytes() and gm.tobytes() == gm2.tobytes()
+    dx = rng.normal(size=(n, 3))
+    dm = rng.normal(size=n) * 1e-4
+    h = 1e-6
+
+    def L(xx, mm):
+        a, p, _ = oracle_mod.force(xx, mm, eps)
+        return float((ga * a).sum() + (gp * p).sum())
+
+    x64, m64 = x32.astype(np.float64), m32.astype(np.float64)
+    jvp = (L(x64 + h * dx, m64 + h * dm) - L(x64 - h * dx, m64 - h * dm)) / (2 * h)
+    vjp = float((gx.astype(np.float64) * dx).sum() + (gm.astype(np.float64) * dm).sum())
+    assert vjp == pytest.approx(jvp, rel=1e-4)
+
+
+def test_autograd_function_matches_kernel(nb, ctx):
+    import torch
+    from paper_0904_3659_gb300.autograd import NBForce
+    n = 1500
+    x, _, m = workloads.plummer(n, seed=11)
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x.astype(np.float32)).to(dev).requires_grad_(True)
+    mt = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
+    rng = np.random.default_rng(12)
+    ga = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).to(dev)
+    gp = torch.from_numpy(rng.normal(size=n).astype(np.float32)).to(dev)
+    a, p = NBForce.apply(xt, mt, 0.02, 0, ctx)
+    ((a * ga).sum() + (p * gp).sum()).backward()
+    gx, gm = gpu_vjp(nb, ctx, x.astype(np.float32), m.astype(np.float32), np.float32(0.02),
+                     ga.cpu().numpy(), gp.cpu().numpy())
+    assert xt.grad.cpu().numpy().tobytes() == gx.tobytes()
+    assert mt.grad.cpu().numpy().tobytes() == gm.tobytes()
+
+
+def _trajectory_grad_check(nb, ctx, oracle_mod, n, eps, dt, steps, ncoords, seed):
+    """Gradients of L = sum |x(T) - y|^2 through `steps` KDK steps with
+    checkpoints every 8 steps, from the adjoint kernel, against (1) the FP64
+    reverse-mode adjoint of the oracle's trajectory for every coordinate and
+    (2) central FP64 finite differences of the oracle's trajectory for
+    `ncoords` random coordinates (1e-4 relative). Steps: 1e-5 for x and v, 1e-3 m_i for a
+    mass (smaller mass steps lose digits to cancellation in L)."""
+    import torch
+    from paper_0904_3659_gb300.autograd import leapfrog
+    dev = torch.device("cuda:0")
+    x0, v0, m = workloads.plummer(n, seed=seed)
+    m = m.astype(np.float32).astype(np.float64)
+    y = workloads.targets(x0, seed=1)
+    xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
+    vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
+    mt = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
+    yt = torch.from_numpy(y).to(dev)
+    xT, _ = leapfrog(xt, vt, mt, eps, dt, steps, checkpoint_every=8, nbctx=ctx)
+    loss = ((xT - yt) ** 2).sum()
+    loss.backward()
+    grads = {"x": xt.grad.cpu().numpy(), "v": vt.grad.cpu().numpy(),
+             "m": mt.grad.cpu().numpy().astype(np.float64)}
+
+    xT64, _, _ = oracle_mod.leapfrog(x0, v0, m, eps, dt, steps)
+    ref = dict(zip("xvm", oracle_mod.leapfrog_grad(x0, v0, m, eps, dt, steps, 2 * (xT64 - y))))
+    # Every coordinate: FP32 rounding in strongly cancelling sums leaves a few
+    # outliers (a mass gradient whose terms nearly cancel), so the bound is on
+    # the 99.9th percentile (1e-4) and on the maximum (1e-3).
+    for kind in "xvm":
+        r = ref[kind]
+        rel = np.abs(grads[kind] - r) / np.maximum(np.abs(r), 1e-3 * np.abs(r).max())
+        assert np.percentile(rel, 99.9) <= 1e-4 and rel.max() <= 1e-3, (kind, rel.max())
+
+    def L(xx, vv, mm):
+        xT_, _, _ = oracle_mod.leapfrog(xx, vv, mm, eps, dt, steps)
+        return float(((xT_ - y) ** 2).sum())
+
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for k in range(ncoords):
+        kind = ["x", "v", "m"][k % 3]
+        if kind == "m":
+            i = int(rng.integers(n))
+            h = 1e-3 * float(m[i])
+            mp_, mm_ = m.copy(), m.copy()
+            mp_[i] += h
+            mm_[i] -= h
+            fd = (L(x0, v0, mp_) - L(x0, v0, mm_)) / (2 * h)
+            g = float(grads["m"][i])
+        else:
+            i, c = int(rng.integers(n)), int(rng.integers(3))
+            h = 1e-5
+            base = x0 if kind == "x" else v0
+            bp, bm = base.copy(), base.copy()
+            bp[i, c] += h
+            bm[i, c] -= h
+            if kind == "x":
+                fd = (L(bp, v0, m) - L(bm, v0, m)) / (2 * h)
+            else:
+                fd = (L(x0, bp, m) - L(x0, bm, m)) / (2 * h)
+            g = float(grads[kind][i, c])
+        scale = max(abs(fd), 1e-3 * np.abs(grads[kind]).max())
+        err = abs(g - fd) / scale
+        worst = max(worst, err)
+        assert err <= 1e-4, (kind, k, g, fd)
+    return worst
+
+
+def test_trajectory_gradient_small(nb, ctx, oracle_mod):
+    # N = 512 Plummer, eps = 1/64, 64 KDK steps of dt = 1/512, checkpoints
+    # every 8 steps, loss = sum |x(T) - y|^2: 15 coordinates of x0, v0, m.
+    _trajectory_grad_check(nb, ctx, oracle_mod, 512, np.float32(1.0 / 64), 1.0 / 512, 64, 15, 4)
+
+
+def test_trajectory_gradient_plummer16384(nb, ctx, oracle_mod):
+    # The full workload (N = 16384, eps = 1/64, 64 steps of dt = 1/512,
+    # checkpoints every 8): each FP64 oracle trajectory takes seconds, so 3
+    # coordinates by default; NB_FULL_ADJOINT_CHECK=1 checks all 32.
+    w = workloads.WORKLOADS["plummer16384_adjoint64"]
+    ncoords = w["fd_coords"] if os.environ.get("NB_FULL_ADJOINT_CHECK") else 3
+    _trajectory_grad_check(nb, ctx, oracle_mod, w["n"], np.float32(w["eps"]), w["dt"], w["steps"],
+                           ncoords, w["seed"])
+
+
+def test_checkpointing_does_not_change_gradients(nb, ctx):
+    import torch
+    from paper_0904_3659_gb300.autograd import leapfrog
+    dev = torch.device("cuda:0")
+    x0, v0, m = workloads.plummer(700, seed=13)
+    out = []
+    for every in (0, 8, 5):
+        xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
+        vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
+        mt = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
+        xT, vT = leapfrog(xt, vt, mt, np.float32(0.02), 1.0 / 256, 20, checkpoint_every=every,
+                          nbctx=ctx)
+        (xT.square().sum() + vT.square().sum()).backward()
+        out.append((xt.grad.cpu().numpy(), vt.grad.cpu().numpy(), mt.grad.cpu().numpy()))
+    # Recomputed segments give the same values; only the order in which
+    # autograd adds gradient contributions may differ.
+    for o in out[1:]:
+        for u, w in zip(out[0], o):
+            np.testing.assert_allclose(w, u, rtol=1e-12, atol=1e-14)
