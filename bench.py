@@ -199,6 +199,144 @@ def oracle_errors(a, p, ref):
 
 
 # --------------------------------------------------------------------------
+# the other workloads, reported beside the headline (each a dict)
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def extra_leapfrog(nb, ctx, dev, torch):
+    """N = 65536 Plummer, eps = 1/128: 16 KDK steps of dt = 1/256 (graph
+    replayed), plain and compensated; energy drift and momentum."""
+    w = workloads.WORKLOADS["plummer65536_kdk16"]
+    x0, v0, m = workloads.plummer(w["n"], seed=w["seed"])
+    n, eps, dt, steps = w["n"], np.float32(w["eps"]), w["dt"], w["steps"]
+    stream = torch.cuda.Stream(dev)
+    out = {"workload": "plummer65536_kdk16", "n": n, "steps": steps}
+    for mode, name in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
+        x = torch.from_numpy(x0.copy()).to(dev)
+        v = torch.from_numpy(v0.copy()).to(dev)
+        mt = torch.from_numpy(m.astype(np.float32)).to(dev)
+        a = torch.zeros((n, 3), dtype=torch.float32, device=dev)
+        p = torch.zeros(n, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        E0 = sum(nb.nb_energy(ctx, x, v, mt, n, eps, mode, stream))
+        P0 = (torch.from_numpy(m)[:, None] * torch.from_numpy(v0)).sum(0).numpy()
+        nb.nb_leapfrog_step(ctx, x, v, mt, a, p, n, eps, dt, 0, 0, mode, stream)  # a(t0)
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        nb.nb_leapfrog_step(ctx, x, v, mt, a, p, n, eps, dt, steps, 1, mode, stream)
+        e1.record(stream)
+        nb.nb_synchronize(ctx, stream)
+        ms = e0.elapsed_time(e1)
+        E1 = sum(nb.nb_energy(ctx, x, v, mt, n, eps, mode, stream))
+        v1 = v.cpu().numpy()
+        P1 = (m[:, None] * v1).sum(0)
+        out[name] = {"ms_per_step": ms / steps, "gint_s": n * n * steps / (ms * 1e-3) / 1e9,
+                     "rel_energy_drift": abs(E1 - E0) / abs(E0),
+                     "momentum_change": float(np.abs(P1 - P0).max()),
+                     "momentum_scale": float((m[:, None] * np.abs(v1)).sum())}
+    return out
+
+
+def extra_batched(nb, ctx, dev, torch, plain_rate):
+    """1024 clusters (N log-uniform in [32, 4096]): one nb_force_batched
+    launch, and 32 graph-replayed batched KDK steps."""
+    w = workloads.WORKLOADS["clusters1024_kdk32"]
+    cl = workloads.clusters(w["n_clusters"], seed=w["seed"], nmin=w["nmin"], nmax=w["nmax"])
+    n, C = cl.x.shape[0], len(cl.sizes)
+    pairs = float((cl.sizes.astype(np.float64) ** 2).sum())
+    x = torch.from_numpy(cl.x.astype(np.float32)).to(dev)
+    mt = torch.from_numpy(cl.m.astype(np.float32)).to(dev)
+    off = torch.from_numpy(cl.offsets).to(dev)
+    eps = torch.from_numpy(cl.eps.astype(np.float32)).to(dev)
+    a = torch.empty((n, 3), device=dev)
+    p = torch.empty(n, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    for _ in range(3):
+        nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p, nb.NB_PLAIN, stream)
+    reps = 10
+    e0, e1 = _events(torch)
+    e0.record(stream)
+    for _ in range(reps):
+        nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p, nb.NB_PLAIN, stream)
+    e1.record(stream)
+    nb.nb_synchronize(ctx, stream)
+    ms = e0.elapsed_time(e1) / reps
+    rate = pairs / (ms * 1e-3) / 1e9
+    x64 = torch.from_numpy(cl.x.copy()).to(dev)
+    v64 = torch.from_numpy(cl.v.copy()).to(dev)
+    torch.cuda.synchronize(dev)
+    steps = w["steps"]
+    nb.nb_leapfrog_batched_step(ctx, x64, v64, mt, off, C, n, eps, a, p, w["dt"], 0, 0,
+                                nb.NB_PLAIN, stream)
+    e0, e1 = _events(torch)
+    e0.record(stream)
+    nb.nb_leapfrog_batched_step(ctx, x64, v64, mt, off, C, n, eps, a, p, w["dt"], steps, 1,
+                                nb.NB_PLAIN, stream)
+    e1.record(stream)
+    nb.nb_synchronize(ctx, stream)
+    ms_lf = e0.elapsed_time(e1)
+    return {"workload": "clusters1024_kdk32", "clusters": C, "particles": n,
+            "interactions_per_eval": pairs, "ms_per_eval": ms, "gint_s": rate,
+            "fraction_of_plain_rate": rate / plain_rate,
+            "kdk32_ms_per_step": ms_lf / steps,
+            "kdk32_gint_s": pairs * steps / (ms_lf * 1e-3) / 1e9}
+
+
+def extra_adjoint(nb, ctx, dev, torch, plain_rate):
+    """N = 16384 Plummer, eps = 1/64: the VJP pair kernel's rate, and one
+    64-step differentiable trajectory (forward + backward, checkpoints every 8)."""
+    from paper_0904_3659_gb300.autograd import leapfrog
+    w = workloads.WORKLOADS["plummer16384_adjoint64"]
+    n, eps = w["n"], np.float32(w["eps"])
+    x0, v0, m = workloads.plummer(n, seed=w["seed"])
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(x0.astype(np.float32)).to(dev)
+    mt = torch.from_numpy(m.astype(np.float32)).to(dev)
+    ga = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).to(dev)
+    gp = torch.from_numpy(rng.normal(size=n).astype(np.float32)).to(dev)
+    gx = torch.empty((n, 3), device=dev)
+    gm = torch.empty(n, device=dev)
+    a = torch.empty((n, 3), device=dev)
+    p = torch.empty(n, device=dev)
+    for _ in range(3):
+        nb.nb_force_vjp(ctx, x, mt, n, eps, ga, gp, gx, gm)
+        nb.nb_force(ctx, x, mt, n, eps, a, p)
+    reps = 20
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(reps):
+        nb.nb_force_vjp(ctx, x, mt, n, eps, ga, gp, gx, gm)
+    e1.record()
+    f0, f1 = _events(torch)
+    f0.record()
+    for _ in range(reps):
+        nb.nb_force(ctx, x, mt, n, eps, a, p)
+    f1.record()
+    nb.nb_synchronize(ctx)
+    vjp_ms = e0.elapsed_time(e1) / reps
+    fwd_ms = f0.elapsed_time(f1) / reps
+    xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
+    vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
+    mg = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
+    yt = torch.from_numpy(workloads.targets(x0, seed=w["target_seed"])).to(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    xT, _ = leapfrog(xt, vt, mg, eps, w["dt"], w["steps"], checkpoint_every=w["checkpoint"],
+                     nbctx=ctx)
+    ((xT - yt) ** 2).sum().backward()
+    torch.cuda.synchronize(dev)
+    traj_s = time.perf_counter() - t0
+    return {"workload": "plummer16384_adjoint64", "n": n,
+            "vjp_ms": vjp_ms, "vjp_gpair_s": n * n / (vjp_ms * 1e-3) / 1e9,
+            "forward_ms_same_n": fwd_ms,
+            "vjp_fraction_of_plain_rate": (n * n / (vjp_ms * 1e-3) / 1e9) / plain_rate,
+            "trajectory_grad_s": traj_s}
+
+
+# --------------------------------------------------------------------------
 # our arm
 
 def run_ours(args):
@@ -340,6 +478,7 @@ def run_ours(args):
         "compensated": {"value": value_comp / 1e9, "unit": "G-int/s", "ms_per_step": ms_comp,
                         "slowdown_vs_plain": ms_comp / ms_plain,
                         "tile": list(tiles.get(nb.NB_COMPENSATED, tiles[nb.NB_PLAIN]).as_tuple()),
+                        "gpu_launches": 3 * args.steps,
                         "pair_ms": comp_pair_ms},
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in plain_k.items()},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G-int/s",
@@ -352,9 +491,18 @@ def run_ours(args):
         "e2e": ({"value": interactions * world / (e2e_ms_max * 1e-3) / 1e9, "unit": "G-int/s",
                  "h2d_bytes_per_step": int(x32.nbytes + m32.nbytes),
                  "d2h_bytes_per_step": int(4 * n * 3 + 4 * n)} if e2e_ms else None),
-        "gpu_launches": 3 * args.steps * 2,
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    if args.extras:
+        plain_rate = value / world / 1e9
+        for key, fn in (("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch)),
+                        ("batched", lambda: extra_batched(nb, ctx, dev, torch, plain_rate)),
+                        ("adjoint", lambda: extra_adjoint(nb, ctx, dev, torch, plain_rate))):
+            try:
+                out[key] = fn()
+            except Exception as e:  # reported in the line, the headline stands
+                out[key] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_cpu_baseline:
         rows = workloads.sample_rows(n, w["sample"], w["sample_seed"])
         rate, sample, ref = cpu_oracle_rate(x32, m32, eps, target_s=args.cpu_seconds,
@@ -418,6 +566,66 @@ def run_reference(args):
     return out
 
 
+def run_case(args):
+    """One kernel class at a small size, for profiler captures: `warmup`
+    untimed launches then `steps` timed ones; prints one JSON line."""
+    import torch
+    import paper_0904_3659_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    case = args.case
+    if case in ("pair", "comp"):
+        n = args.n or (1 << 17)
+        x32, m32 = make_inputs(n, 0)
+        x = torch.from_numpy(x32).to(dev)
+        mt = torch.from_numpy(m32).to(dev)
+        a = torch.empty((n, 3), device=dev)
+        p = torch.empty(n, device=dev)
+        mode = nb.NB_PLAIN if case == "pair" else nb.NB_COMPENSATED
+        if args.tile:
+            nb.nb_set_tile(ctx, mode, tuple(int(v) for v in args.tile.split(",")))
+        fn = lambda: nb.nb_force(ctx, x, mt, n, 1.0 / 256, a, p, mode)
+        units = float(n) * n
+    elif case == "batched":
+        w = workloads.WORKLOADS["clusters1024_kdk32"]
+        cl = workloads.clusters(w["n_clusters"], seed=w["seed"], nmin=w["nmin"], nmax=w["nmax"])
+        n, C = cl.x.shape[0], len(cl.sizes)
+        x = torch.from_numpy(cl.x.astype(np.float32)).to(dev)
+        mt = torch.from_numpy(cl.m.astype(np.float32)).to(dev)
+        off = torch.from_numpy(cl.offsets).to(dev)
+        eps = torch.from_numpy(cl.eps.astype(np.float32)).to(dev)
+        a = torch.empty((n, 3), device=dev)
+        p = torch.empty(n, device=dev)
+        fn = lambda: nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p)
+        units = float((cl.sizes.astype(np.float64) ** 2).sum())
+    elif case == "vjp":
+        n = args.n or 16384
+        x32, m32 = make_inputs(n, 0)
+        rng = np.random.default_rng(5)
+        x = torch.from_numpy(x32).to(dev)
+        mt = torch.from_numpy(m32).to(dev)
+        ga = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).to(dev)
+        gp = torch.from_numpy(rng.normal(size=n).astype(np.float32)).to(dev)
+        gx = torch.empty((n, 3), device=dev)
+        gm = torch.empty(n, device=dev)
+        fn = lambda: nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, gp, gx, gm)
+        units = float(n) * n
+    else:
+        raise SystemExit(f"unknown case {case}")
+    for _ in range(args.warmup):
+        fn()
+    nb.nb_synchronize(ctx)
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    nb.nb_synchronize(ctx)
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": case, "n": n, "ms": ms, "g_units_s": units / (ms * 1e-3) / 1e9}),
+          flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,10 +641,16 @@ def main(argv=None):
     ap.add_argument("--tile-comp", default="", help="compensated tile: threads,ipt,jtile,stages")
     ap.add_argument("--plain-only", action="store_true")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--case", choices=["pair", "comp", "batched", "vjp"], default="",
+                    help="time one kernel class at a small size (profiler captures)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the leap-frog, batched and adjoint workloads")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     return run_ours(args)
 
 
