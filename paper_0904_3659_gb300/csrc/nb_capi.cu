@@ -224,6 +224,57 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     return NB_OK;
 }
 
+nb_status reserve_frames(nb_ctx *ctx, int64_t n) {
+    const PairVariant &v = *frames_variant(n);
+    const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
+    cudaError_t e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, plan.partial_bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (partial sums)");
+    return NB_OK;
+}
+
+nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, const int32_t *perm,
+                           int64_t n, float eps, float *a, float *p, cudaStream_t st) {
+    const PairVariant &v = *frames_variant(n);
+    const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
+    nb_status rs = reserve_frames(ctx, n);
+    if (rs != NB_OK) return rs;
+    PairArgs pa{};
+    pa.jp = jp;
+    pa.partial = static_cast<float4 *>(ctx->d_partial);
+    pa.err = ctx->d_err;
+    pa.njt = plan.njt;
+    pa.units = plan.units;
+    pa.grid = plan.grid;
+    pa.maxseg = plan.maxseg;
+    pa.eps2 = eps * eps;
+    pa.fault_unit = ctx->fault_unit;
+    pa.wait_ns = ctx->wait_ns;
+    pa.cref = cref;
+    cudaError_t e;
+    {
+        TimedLaunch t(ctx, K_PAIR, st);
+        e = v.launch(pa, plan.grid, v.smem, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pair kernel launch (frames)");
+    ReduceArgs ra{};
+    ra.partial = pa.partial;
+    ra.a = a;
+    ra.p = p;
+    ra.n = n;
+    ra.njt = plan.njt;
+    ra.units = plan.units;
+    ra.grid = plan.grid;
+    ra.maxseg = plan.maxseg;
+    ra.ib = plan.ib;
+    ra.perm = perm;
+    {
+        TimedLaunch t(ctx, K_REDUCE, st);
+        e = launch_reduce(ra, true, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch (frames)");
+    return NB_OK;
+}
+
 nb_status check_common(nb_ctx *ctx, int64_t n, float eps, int mode) {
     if (n < 0) return fail(ctx, NB_ERR_ARG, "n must be >= 0");
     if (!std::isfinite(eps) || !(eps > 0.f)) return fail(ctx, NB_ERR_ARG, "eps must be finite and > 0");

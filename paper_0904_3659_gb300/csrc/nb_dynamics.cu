@@ -18,6 +18,7 @@
 #include "nb_device.cuh"
 #include "nb_ext.h"
 #include "nb_internal.h"
+#include "nb_order.h"
 
 namespace nbk {
 
@@ -67,6 +68,20 @@ __global__ void kick_drift_pack_kernel(double *__restrict__ x, double *__restric
         xn[c] = xc;
     }
     pack_one(jp, i, xn[0], xn[1], xn[2], m[i]);
+}
+
+// Kicks and drift without packing (the compensated path packs offsets from
+// reference points in a separate kernel).
+__global__ void kick_drift_kernel(double *__restrict__ x, double *__restrict__ v,
+                                  const float *__restrict__ a, int64_t n, double dt, int kick_back) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const double h = 0.5 * dt, g = -(double)a[k];
+    double vc = v[k];
+    if (kick_back) vc = vc + h * g;  // Eq. (3) of the previous step
+    vc = vc + h * g;                 // Eq. (1)
+    v[k] = vc;
+    x[k] = x[k] + dt * vc;           // Eq. (2)
 }
 
 __global__ void kick_kernel(double *__restrict__ v, const float *__restrict__ a, int64_t n,
@@ -124,7 +139,7 @@ using namespace nbx;
 
 namespace {
 
-enum Slot { S_JP = 0, S_A = 1, S_P = 2, S_EBLK = 3, S_EOUT = 4 };
+enum Slot { S_JP = 0, S_A = 1, S_P = 2, S_EBLK = 3, S_EOUT = 4, S_PERM = 11 };
 
 void *slot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
 
@@ -146,6 +161,38 @@ nb_status reserve_force(nb_ctx *ctx, int64_t n, bool comp) {
 
 int64_t padded(int64_t n) { return round_up(std::max<int64_t>(n, 1), kPad); }
 
+// Compensated path for FP64 state: permutation (Morton order) and, per force
+// evaluation, reference-point offsets. One buffer holds the permutation, the
+// ordering scratch and the reference points.
+struct Frames {
+    int32_t *perm = nullptr;
+    void *order_scratch = nullptr;
+    float4 *cref = nullptr;
+};
+
+nb_status reserve_frames_state(nb_ctx *ctx, int64_t n, Frames *f) {
+    const size_t perm_bytes = round_up((int64_t)order_pow2(n) * sizeof(int32_t), 256);
+    const size_t order_bytes = round_up((int64_t)order_scratch_bytes(n), 256);
+    const size_t cref_bytes = (size_t)(padded(n) / 256) * sizeof(float4);
+    nb_status st = ensure_slot(ctx, S_PERM, perm_bytes + order_bytes + cref_bytes);
+    if (st != NB_OK) return st;
+    if ((st = reserve_frames(ctx, n)) != NB_OK) return st;
+    unsigned char *base = static_cast<unsigned char *>(slot(ctx, S_PERM));
+    f->perm = reinterpret_cast<int32_t *>(base);
+    f->order_scratch = base + perm_bytes;
+    f->cref = reinterpret_cast<float4 *>(base + perm_bytes + order_bytes);
+    return NB_OK;
+}
+
+// Eq. (gravity) from FP64 positions through the frames (order already set).
+nb_status force_frames(nb_ctx *ctx, const double *x, const float *m, const Frames &f, int64_t n,
+                       float eps, float *a, float *p, cudaStream_t st) {
+    JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
+    cudaError_t e = launch_frames_pack(x, m, f.perm, n, padded(n), 256, jp, f.cref, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frames pack launch");
+    return run_force_frames(ctx, jp, f.cref, f.perm, n, eps, a, p, st);
+}
+
 // Enqueue the steps 1 .. nsteps-1 body: fused kicks+drift+pack, force.
 nb_status steady_step(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
                       int64_t n, float eps, double dt, bool comp, cudaStream_t st) {
@@ -155,6 +202,56 @@ nb_status steady_step(nb_ctx *ctx, double *x, double *v, const float *m, float *
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "leap-frog update launch");
     return run_force(ctx, nullptr, nullptr, jp, n, eps, a, p, comp, st);
+}
+
+// The compensated leap-frog: the order is fixed for the call (from the entry
+// positions); every force evaluation re-packs offsets from the tiles'
+// reference points. Steps after the first are replayed from a graph.
+nb_status leapfrog_frames(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
+                          int64_t n, float eps, double dt, int nsteps, int a_valid, cudaStream_t s) {
+    Frames f;
+    nb_status st = reserve_frames_state(ctx, n, &f);
+    if (st != NB_OK) return st;
+    cudaError_t e = launch_spatial_order(x, n, f.order_scratch, f.perm, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ordering launch");
+    if (!a_valid && (st = force_frames(ctx, x, m, f, n, eps, a, p, s)) != NB_OK) return st;
+    if (nsteps == 0) return NB_OK;
+    const unsigned nb3 = blocks_for(3 * n, 256);
+    auto step = [&](int kick_back) -> nb_status {
+        kick_drift_kernel<<<nb3, 256, 0, s>>>(x, v, a, n, dt, kick_back);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "leap-frog update launch");
+        return force_frames(ctx, x, m, f, n, eps, a, p, s);
+    };
+    if ((st = step(0)) != NB_OK) return st;
+    const int rest = nsteps - 1;
+    if (rest >= 2 && s != nullptr) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
+        const bool timing = ctx_set_timing(ctx, false);
+        nb_status cst = step(1);
+        ctx_set_timing(ctx, timing);
+        e = cudaStreamEndCapture(s, &graph);
+        if (cst != NB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cst;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+        for (int k = 0; k < rest && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    } else {
+        for (int k = 0; k < rest; ++k)
+            if ((st = step(1)) != NB_OK) return st;
+    }
+    kick_kernel<<<nb3, 256, 0, s>>>(v, a, n, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "kick launch");
+    return NB_OK;
 }
 
 }  // namespace
@@ -185,6 +282,8 @@ nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, fl
     }
     JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
     cudaError_t e;
+
+    if (comp) return leapfrog_frames(ctx, x, v, m, a, pbuf, n, eps, dt, nsteps, a_valid, s);
 
     if (!a_valid) {
         pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
@@ -256,10 +355,19 @@ nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *
     JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
     float *abuf = static_cast<float *>(slot(ctx, S_A));
     float *pbuf = static_cast<float *>(slot(ctx, S_P));
-    pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "pack launch");
-    if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, abuf, pbuf, comp, s)) != NB_OK) return st;
+    cudaError_t e;
+    if (comp) {
+        Frames f;
+        if ((st = reserve_frames_state(ctx, n, &f)) != NB_OK) return st;
+        e = launch_spatial_order(x, n, f.order_scratch, f.perm, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ordering launch");
+        if ((st = force_frames(ctx, x, m, f, n, eps, abuf, pbuf, s)) != NB_OK) return st;
+    } else {
+        pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "pack launch");
+        if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, abuf, pbuf, comp, s)) != NB_OK) return st;
+    }
     double2 *blk = static_cast<double2 *>(slot(ctx, S_EBLK));
     double2 *out = static_cast<double2 *>(slot(ctx, S_EOUT));
     energy_partial_kernel<<<nblk, kEnergyThreads, 0, s>>>(v, m, pbuf, n, blk);

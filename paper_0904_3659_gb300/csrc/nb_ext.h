@@ -51,6 +51,15 @@ cudaError_t ensure_buffer(void **ptr, size_t *cap, size_t bytes);
 int resident_ctas(nb_ctx *ctx, const nbk::PairVariant &v);
 const nbk::PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp);
 
+// Frame path (compensated, FP64 state): pair kernel on particles packed in
+// perm order as offsets from per-tile reference points cref, combine
+// scattering result k to particle perm[k].
+nb_status run_force_frames(nb_ctx *ctx, const nbk::JPart *jp, const float4 *cref,
+                           const int32_t *perm, int64_t n, float eps, float *a, float *p,
+                           cudaStream_t st);
+// Allocate the frame path's partial sums for n (before any graph capture).
+nb_status reserve_frames(nb_ctx *ctx, int64_t n);
+
 // pack (unless prepacked) -> pair -> combine, enqueued on st.
 nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const nbk::JPart *prepacked,
                     int64_t n, float eps, float *a, float *p, bool comp, cudaStream_t st);

@@ -39,6 +39,7 @@ struct PairArgs {
     float eps2;            // eps^2 in FP32
     int64_t fault_unit;    // test hook: unit whose copy is never issued (-1: none)
     uint64_t wait_ns;      // limit of one bounded barrier wait
+    const float4 *cref;    // per-j-tile reference points (frame variants only)
 };
 
 // Arguments of the deterministic cross-CTA combine.
@@ -52,6 +53,7 @@ struct ReduceArgs {
     int grid;
     int maxseg;
     int ib;
+    const int32_t *perm;   // if set, result k is written to particle perm[k]
 };
 
 inline bool same_tile(const nb_tile &a, const nb_tile &b) {
@@ -70,6 +72,9 @@ struct PairVariant {
 };
 
 // Registry of compiled variants (nb_pair.cu).
+// Frame variants: compensated kernels that re-centre on per-tile reference
+// points (positions packed as offsets, see nb_order.cu).
+const PairVariant *frames_variant(int64_t n);
 int pair_variant_count(bool comp);
 const PairVariant *pair_variant(bool comp, int idx);
 const PairVariant *pair_variant_find(bool comp, const nb_tile &t);

@@ -76,8 +76,12 @@ __global__ void pack_f32_kernel(const float *__restrict__ x, const float *__rest
 //                 touched once per tile; frees 8-16 registers per i-particle)
 //   MIX           which op groups of an interaction run packed (see kMix*)
 //   COMP          Kahan-compensated running sums (NB_COMPENSATED)
+//   FR            positions are packed as FP32 offsets from per-j-tile
+//                 reference points args.cref; before each tile the thread
+//                 re-centres its i-particles on that tile's point:
+//                 x~_i = delta_i + (c_I - c_J), I the tile holding i.
 template <int THREADS, int IPT, int JT, int STAGES, int UNR, int MINB, int REL, int ACCS, int MIX,
-          bool COMP>
+          bool COMP, bool FR>
 __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args) {
     static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
     constexpr int P = IPT / 2;
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
     }
 
     float2 xi[P], yi[P], zi[P];
+    float2 cix[P], ciy[P], ciz[P];  // FR: reference point of each i's own tile
     float2 sum[P][4], cmp[P][4];
     const float2 eps2 = splat2(args.eps2);
     const float2 zero2 = splat2(0.f);
@@ -196,6 +201,12 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
                 xi[q] = make_float2(-A0.x, -A1.x);
                 yi[q] = make_float2(-A0.z, -A1.z);
                 zi[q] = make_float2(-B0.x, -B1.x);
+                if (FR) {
+                    const float4 c0 = args.cref[i0 / JT], c1 = args.cref[i1 / JT];
+                    cix[q] = make_float2(c0.x, c1.x);
+                    ciy[q] = make_float2(c0.y, c1.y);
+                    ciz[q] = make_float2(c0.z, c1.z);
+                }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     put_sum(q, r, zero2);
@@ -218,6 +229,25 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
 
+        // Positions of the i-particles in the frame of this j-tile.
+        float2 xr[P], yr[P], zr[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            xr[q] = xi[q];
+            yr[q] = yi[q];
+            zr[q] = zi[q];
+        }
+        if (FR) {
+            const float4 cj = args.cref[jt];
+            const float2 ncx = splat2(-cj.x), ncy = splat2(-cj.y), ncz = splat2(-cj.z);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                xr[q] = add2(xi[q], add2(cix[q], ncx));
+                yr[q] = add2(yi[q], add2(ciy[q], ncy));
+                zr[q] = add2(zi[q], add2(ciz[q], ncz));
+            }
+        }
+
         const int64_t ibase = b * IB, jbase = jt * JT;
         int self0[P], self1[P];
         if (jbase < ibase + IB && ibase < jbase + JT) {
@@ -226,9 +256,9 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
                 self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
                 self1[q] = self0[q] + THREADS;
             }
-            tile_pass<P, JT, 1, true, MIX>(T, xi, yi, zi, acc, eps2, self0, self1);
+            tile_pass<P, JT, 1, true, MIX>(T, xr, yr, zr, acc, eps2, self0, self1);
         } else {
-            tile_pass<P, JT, UNR, false, MIX>(T, xi, yi, zi, acc, eps2, self0, self1);
+            tile_pass<P, JT, UNR, false, MIX>(T, xr, yr, zr, acc, eps2, self0, self1);
         }
 
         if (REL == 1) {
@@ -304,10 +334,11 @@ __global__ void reduce_plain_kernel(const ReduceArgs r) {
         az = __fadd_rn(az, v.z);
         pp = __fadd_rn(pp, v.w);
     }
-    r.a[3 * i + 0] = 0.25f * ax;
-    r.a[3 * i + 1] = 0.25f * ay;
-    r.a[3 * i + 2] = 0.25f * az;
-    r.p[i] = pp;
+    const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
+    r.a[3 * o + 0] = 0.25f * ax;
+    r.a[3 * o + 1] = 0.25f * ay;
+    r.a[3 * o + 2] = 0.25f * az;
+    r.p[o] = pp;
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -340,10 +371,11 @@ __global__ void reduce_comp_kernel(const ReduceArgs r) {
             E[q] = __fadd_rn(E[q], __fsub_rn(e, l[q]));  // segment value = hi - lo
         }
     }
-    r.a[3 * i + 0] = 0.25f * __fadd_rn(S[0], E[0]);
-    r.a[3 * i + 1] = 0.25f * __fadd_rn(S[1], E[1]);
-    r.a[3 * i + 2] = 0.25f * __fadd_rn(S[2], E[2]);
-    r.p[i] = __fadd_rn(S[3], E[3]);
+    const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
+    r.a[3 * o + 0] = 0.25f * __fadd_rn(S[0], E[0]);
+    r.a[3 * o + 1] = 0.25f * __fadd_rn(S[1], E[1]);
+    r.a[3 * o + 2] = 0.25f * __fadd_rn(S[2], E[2]);
+    r.p[o] = __fadd_rn(S[3], E[3]);
 }
 
 // Synthetic inputs for tuning runs (timing only; values do not matter
@@ -363,9 +395,9 @@ __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed
 
 // ---------------------------------------------------------------------------
 // Launchers and the registry of compiled shapes.
-template <int T, int I, int J, int S, int U, int M, int R, int A, int X, bool C>
+template <int T, int I, int J, int S, int U, int M, int R, int A, int X, bool C, bool F>
 static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
-    pair_kernel<T, I, J, S, U, M, R, A, X, C><<<grid, T, smem, st>>>(a);
+    pair_kernel<T, I, J, S, U, M, R, A, X, C, F><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -376,9 +408,10 @@ constexpr size_t pair_smem() {
            (size_t)S * sizeof(uint64_t) + (2 * S + 1) * sizeof(int);
 }
 
-#define NB_VARIANT(T, I, J, S, U, M, R, A, X, C)                                                \
-    {{T, I, J, S, U, M, R, A, X}, C, (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, C>,      \
-     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, C>}
+#define NB_VARIANT_F(T, I, J, S, U, M, R, A, X, C, F)                                           \
+    {{T, I, J, S, U, M, R, A, X}, C, (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, C, F>,   \
+     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, C, F>}
+#define NB_VARIANT(T, I, J, S, U, M, R, A, X, C) NB_VARIANT_F(T, I, J, S, U, M, R, A, X, C, false)
 
 // Plain shapes: entry 0 is the large-n default, entry 1 the small-n default.
 // (Measured on GB300 at N = 2^18 and 2^20: the all-packed mask 63 beats every
@@ -408,7 +441,16 @@ static const PairVariant kComp[] = {
     NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, true),
     NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, true),
 };
+// Frame variants (compensated, per-tile reference points; jtile must be 256,
+// the only tile length the frames pack is compiled for).
+static const PairVariant kFrames[] = {
+    NB_VARIANT_F(128, 6, 256, 3, 8, 1, 0, 1, 63, true, true),  // large n
+    NB_VARIANT_F(64, 4, 256, 3, 4, 1, 0, 1, 63, true, true),   // small n
+};
 #undef NB_VARIANT
+#undef NB_VARIANT_F
+
+const PairVariant *frames_variant(int64_t n) { return n >= (int64_t)1 << 16 ? &kFrames[0] : &kFrames[1]; }
 
 int pair_variant_count(bool comp) {
     return comp ? (int)(sizeof(kComp) / sizeof(kComp[0])) : (int)(sizeof(kPlain) / sizeof(kPlain[0]));

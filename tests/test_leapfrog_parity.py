@@ -173,3 +173,48 @@ def test_plummer65536_kdk16(nb, ctx, stream, mode):
     P = (m.astype(np.float64)[:, None] * v1).sum(0)
     Pscale = (m.astype(np.float64)[:, None] * np.abs(v1)).sum()
     assert np.abs(P).max() < 1e-6 * Pscale
+
+
+def _force_from_fp64(nb, ctx, stream, x64, m, eps, mode):
+    s = State(x64, np.zeros_like(x64), m)
+    s.step(nb, ctx, eps, 0.0, 0, 0, mode, stream)   # a at the entry positions only
+    return s.a.cpu().numpy().astype(np.float64), s.p.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("offset", [0.0, 1000.0])
+def test_fp64_state_force_compensated_frames(nb, ctx, stream, oracle_mod, offset):
+    # Positions held in FP64, the cluster centred at the origin or displaced
+    # to x = 1000. Rounding them to FP32 (plain) costs u |x| absolute in every
+    # x_i - x_j; the compensated path packs offsets from per-tile reference
+    # points of a spatially ordered copy and stays within 1e-6 of the FP64
+    # oracle evaluated on the unrounded positions.
+    n, eps = 65536, np.float32(1.0 / 128)
+    x, _, m = workloads.plummer(n, seed=21)
+    x = x + np.array([offset, 0.0, 0.0])
+    m = m.astype(np.float32)
+    rows = workloads.sample_rows(n, 600, seed=4)
+    ra, rp, ramag = oracle_mod.force_rows(x, m, eps, rows)
+    errs = {}
+    for mode in (0, 1):
+        a, p = _force_from_fp64(nb, ctx, stream, x, m, eps, mode)
+        ea = np.linalg.norm(a[rows] - ra, axis=1) / ramag
+        ep = np.abs(p[rows] - rp) / rp
+        errs[mode] = max(ea.max(), ep.max())
+    assert errs[1] <= 1e-6, errs
+    if offset:
+        assert errs[0] > 1e-5, errs   # the rounding loss the frames remove
+
+
+def test_compensated_leapfrog_deterministic_and_close_to_plain(nb, ctx, stream):
+    n, eps, dt = 6000, np.float32(1.0 / 64), 1.0 / 256
+    x0, v0, m = plummer_state(n, 22)
+    runs = []
+    for _ in range(2):
+        s = State(x0, v0, m)
+        s.step(nb, ctx, eps, dt, 12, 0, 1, stream)
+        runs.append(s)
+    assert runs[0].x.cpu().numpy().tobytes() == runs[1].x.cpu().numpy().tobytes()
+    assert runs[0].a.cpu().numpy().tobytes() == runs[1].a.cpu().numpy().tobytes()
+    sp = State(x0, v0, m)
+    sp.step(nb, ctx, eps, dt, 12, 0, 0, stream)
+    assert np.abs(sp.x.cpu().numpy() - runs[0].x.cpu().numpy()).max() < 1e-8
