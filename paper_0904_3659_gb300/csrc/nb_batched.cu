@@ -23,6 +23,12 @@ using namespace nbdev;
 
 constexpr int kClusterPad = 128;  // >= every batched i-block and j-tile
 constexpr int kPlanThreads = 1024;
+constexpr int kMaxChunks = 4;      // the j-range of an i-block is split into at most this many items
+
+// Chunks an i-block of a cluster with ntiles j-tiles is split into.
+__host__ __device__ __forceinline__ int64_t chunks_of(int64_t ntiles) {
+    return ntiles < kMaxChunks ? ntiles : kMaxChunks;
+}
 
 struct BatchPlanArgs {
     const int64_t *off;   // [C+1] caller's offsets
@@ -31,8 +37,10 @@ struct BatchPlanArgs {
     int64_t cap_padded;   // capacity of the padded particle array
     int64_t cap_items;    // capacity of the item list
     int ib;               // i-block size of the pair kernel
+    int jt;               // j-tile size of the pair kernel
     int64_t *poff;        // [C+1] padded offsets (out)
-    int2 *items;          // [cap_items] (cluster, i-block) (out)
+    int4 *items;          // [cap_items] (cluster, i-block, chunk, chunks) (out)
+    int64_t *ibase;       // [C] index of the cluster's first item (out)
     int *nitems;          // item count (out)
     int *err;             // set if the offsets do not fit the capacities
 };
@@ -91,21 +99,40 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPla
     }
     if (t == 0) P.poff[P.C] = carry;
     const bool fits = carry <= P.cap_padded;
+    // Size classes present (one bit each), so the item pass below visits only those.
+    __shared__ unsigned long long present;
+    if (t == 0) present = 0ull;
+    __syncthreads();
+    for (int64_t c = t; c < P.C; c += kPlanThreads) {
+        const int64_t nc = P.off[c + 1] - P.off[c];
+        const int64_t psz = nc > 0 ? (nc + kClusterPad - 1) / kClusterPad * kClusterPad : 0;
+        if (psz > 0) atomicOr(&present, 1ull << size_class(psz));
+    }
+    __syncthreads();
+    const unsigned long long classes = present;
     // Items, largest size class first; clusters in index order within a class.
     int64_t nit = 0;
     for (int cls = 62; cls >= 0 && fits; --cls) {
+        if (!((classes >> cls) & 1ull)) continue;
         for (int64_t base = 0; base < P.C; base += kPlanThreads) {
             const int64_t c = base + t;
-            int64_t cnt = 0;
+            int64_t cnt = 0, nb = 0, nch = 0;
             if (c < P.C) {
                 const int64_t nc = P.off[c + 1] - P.off[c];
                 const int64_t psz = nc > 0 ? (nc + kClusterPad - 1) / kClusterPad * kClusterPad : 0;
-                if (size_class(psz) == cls) cnt = psz / P.ib;
+                if (size_class(psz) == cls) {
+                    nb = psz / P.ib;
+                    nch = chunks_of(psz / P.jt);
+                    cnt = nb * nch;
+                }
             }
             int64_t total;
             const int64_t ex = block_exclusive_scan(cnt, scan, &total);
+            if (cnt) P.ibase[c] = nit + ex;
             if (nit + total <= P.cap_items)
-                for (int64_t k = 0; k < cnt; ++k) P.items[nit + ex + k] = make_int2((int)c, (int)k);
+                for (int64_t b = 0; b < nb; ++b)
+                    for (int64_t k = 0; k < nch; ++k)
+                        P.items[nit + ex + b * nch + k] = make_int4((int)c, (int)b, (int)k, (int)nch);
             nit += total;
         }
     }
@@ -143,11 +170,10 @@ struct BatchArgs {
     const int64_t *off;
     const int64_t *poff;
     const float *eps;
-    const int2 *items;
+    const int4 *items;
     const int *nitems;
     int *counter;
-    float *a;
-    float *p;
+    float4 *partial;  // [item][words][ib]: one item's sums for its i-block
     int *err;
     uint64_t wait_ns;
 };
@@ -156,30 +182,43 @@ struct StageMeta {
     int item, cluster, iblock, jt, end;
 };
 
-template <int THREADS, int IPT, int JT, int STAGES, bool COMP>
-__global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A) {
+// Warp-level persistent kernel: every warp of a CTA is an independent
+// worker with its own shared-memory stages, barriers and item stream. Lane 0
+// pops (cluster, i-block) items from the device queue, issues the 1-D bulk
+// copies of that cluster's j-tiles, and the whole warp consumes them. A work
+// item is 32 lanes x IPT i-particles (IPT/2 packed pairs per lane), so the
+// item equals the cluster padding and no CTA-wide barrier is needed.
+template <int WARPS, int IPT, int JT, int STAGES, bool COMP>
+__global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArgs A) {
     constexpr int P = IPT / 2;
-    constexpr int IB = THREADS * IPT;
+    constexpr int IB = 32 * IPT;
     constexpr uint32_t TILE_BYTES = JT * sizeof(JPart);
     static_assert(kClusterPad % IB == 0 && kClusterPad % JT == 0, "tiles must divide the padding");
+    constexpr size_t WARP_BYTES = (size_t)STAGES * TILE_BYTES;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    JPart *tiles = reinterpret_cast<JPart *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES);
-    StageMeta *meta = reinterpret_cast<StageMeta *>(full + STAGES);
-    int *issued_at = reinterpret_cast<int *>(meta + STAGES);  // last unit copied into each stage
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    JPart *tiles = reinterpret_cast<JPart *>(smem + warp * WARP_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + WARPS * WARP_BYTES) + warp * STAGES;
+    StageMeta *meta =
+        reinterpret_cast<StageMeta *>(reinterpret_cast<uint64_t *>(smem + WARPS * WARP_BYTES) +
+                                      WARPS * STAGES) + warp * STAGES;
+    int *issued_at = reinterpret_cast<int *>(
+                         reinterpret_cast<StageMeta *>(reinterpret_cast<uint64_t *>(
+                                                           smem + WARPS * WARP_BYTES) +
+                                                       WARPS * STAGES) +
+                         WARPS * STAGES) + warp * STAGES;
 
-    const int tid = threadIdx.x;
-    if (tid == 0) {
+    if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             issued_at[s] = -1;
         }
         fence_mbar_init();
     }
-    __syncthreads();
+    __syncwarp();
 
-    // Producer (thread 0): walks the (item, j-tile) stream, popping items.
+    // Producer state (lane 0): walks the (item, j-tile) stream, popping items.
     int p_item = -1, p_cluster = 0, p_b = 0, p_jt = 0, p_ntiles = 0, p_done = 0;
     int64_t p_base = 0;
     const int nitems = *A.nitems;
@@ -190,13 +229,15 @@ __global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A
             if (it >= nitems) {
                 p_done = 1;
             } else {
-                const int2 w = A.items[it];
+                const int4 w = A.items[it];
                 p_item = it;
                 p_cluster = w.x;
                 p_b = w.y;
-                p_jt = 0;
                 p_base = A.poff[w.x];
-                p_ntiles = (int)((A.poff[w.x + 1] - p_base) / JT);
+                const int ntiles = (int)((A.poff[w.x + 1] - p_base) / JT);
+                // chunk w.z of w.w: tiles [w.z*ntiles/w.w, (w.z+1)*ntiles/w.w)
+                p_jt = (int)((int64_t)w.z * ntiles / w.w);
+                p_ntiles = (int)((int64_t)(w.z + 1) * ntiles / w.w);
             }
         }
         StageMeta mt;
@@ -216,7 +257,7 @@ __global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A
             ++p_jt;
         }
     };
-    if (tid == 0)
+    if (lane == 0)
         for (int kk = 0; kk < STAGES - 1; ++kk) produce(kk);
 
     float2 xi[P], yi[P], zi[P];
@@ -225,38 +266,31 @@ __global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A
     int cur_item = -1, cur_cluster = 0, cur_b = 0;
     float2 eps2 = zero2;
 
+    // The item's sums (and Kahan carries) for its i-block.
     auto write_out = [&]() {
-        const int64_t o = A.off[cur_cluster], nc = A.off[cur_cluster + 1] - o;
+        float4 *dst = A.partial + (int64_t)cur_item * (COMP ? 2 : 1) * IB;
 #pragma unroll
-        for (int q = 0; q < P; ++q)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t li = (int64_t)cur_b * IB + (2 * q + h) * THREADS + tid;
-                if (li >= nc) continue;
-                float v[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float sv = h ? sum[q][r].y : sum[q][r].x;
-                    const float cv = h ? cmp[q][r].y : cmp[q][r].x;
-                    v[r] = COMP ? __fsub_rn(sv, cv) : sv;
-                }
-                const int64_t gi = o + li;
-                A.a[3 * gi + 0] = 0.25f * v[0];
-                A.a[3 * gi + 1] = 0.25f * v[1];
-                A.a[3 * gi + 2] = 0.25f * v[2];
-                A.p[gi] = v[3];
+        for (int q = 0; q < P; ++q) {
+            const int i0 = (2 * q) * 32 + lane, i1 = i0 + 32;
+            dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
+            dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+            if (COMP) {
+                dst[IB + i0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
+                dst[IB + i1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
             }
+        }
     };
 
     int bad = 0;
-    int k = 0;
-    for (;; ++k) {
-        if (__syncthreads_or(bad)) break;
-        if (tid == 0) produce(k + STAGES - 1);
+    for (int k = 0;; ++k) {
+        // All lanes are done with iteration k-1: its stage may be refilled.
+        __syncwarp();
+        if (lane == 0) produce(k + STAGES - 1);
         const int s = k % STAGES;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((k / STAGES) & 1), A.wait_ns)) {
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((k / STAGES) & 1), A.wait_ns)) bad = 1;
+        if (__any_sync(0xffffffffu, bad)) {
             bad = 1;
-            continue;
+            break;
         }
         const StageMeta mt = meta[s];
         if (mt.end) break;
@@ -269,7 +303,7 @@ __global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A
             const int64_t base = A.poff[cur_cluster] + (int64_t)cur_b * IB;
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                const int64_t i0 = base + (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+                const int64_t i0 = base + (2 * q) * 32 + lane, i1 = i0 + 32;
                 const float4 A0 = reinterpret_cast<const float4 *>(A.jp + i0)[0];
                 const float4 B0 = reinterpret_cast<const float4 *>(A.jp + i0)[1];
                 const float4 A1 = reinterpret_cast<const float4 *>(A.jp + i1)[0];
@@ -295,8 +329,8 @@ __global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A
         if (jbase < ibase + IB && ibase < jbase + JT) {
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                self0[q] = ibase + (2 * q) * THREADS + tid - jbase;
-                self1[q] = self0[q] + THREADS;
+                self0[q] = ibase + (2 * q) * 32 + lane - jbase;
+                self1[q] = self0[q] + 32;
             }
             tile_pass<P, JT, 1, true, kMixAll>(T, xi, yi, zi, acc, eps2, self0, self1);
         } else {
@@ -316,16 +350,67 @@ __global__ void __launch_bounds__(THREADS) batched_pair_kernel(const BatchArgs A
                 }
             }
     }
-    bad = __syncthreads_or(bad);
     if (!bad) {
         if (cur_item >= 0) write_out();
         return;
     }
-    if (tid == 0) {
+    if (lane == 0) {
         atomicOr(A.err, kErrTimeout);
+        // Let this warp's copies in flight land before the CTA can exit.
         for (int s = 0; s < STAGES; ++s)
             if (issued_at[s] >= 0)
                 mbar_wait_bounded(&full[s], (uint32_t)((issued_at[s] / STAGES) & 1), A.wait_ns);
+    }
+    __syncwarp();
+}
+
+// Per particle: add the chunk sums of its (cluster, i-block) in chunk order
+// and remove the factor 4 of the acceleration. One block per cluster.
+template <bool COMP>
+__global__ void batch_combine_kernel(const float4 *__restrict__ partial,
+                                     const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
+                                     const int64_t *__restrict__ ibase, int ib, int jt,
+                                     float *__restrict__ a, float *__restrict__ p) {
+    const int64_t c = blockIdx.x;
+    // poff holds the validated padded sizes: all zero when the planner
+    // rejected the offsets, so nothing is written for an invalid batch, and
+    // a valid cluster's real size never exceeds its padded size.
+    const int64_t psz = poff[c + 1] - poff[c];
+    if (psz <= 0) return;
+    const int64_t o = off[c];
+    const int64_t nc = off[c + 1] - o < psz ? off[c + 1] - o : psz;
+    if (nc <= 0) return;
+    const int64_t nch = chunks_of(psz / jt);
+    for (int64_t li = threadIdx.x; li < nc; li += blockDim.x) {
+        const int64_t b = li / ib, w = li - b * ib;
+        const int64_t first = ibase[c] + b * nch;
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t k = 0; k < nch; ++k) {
+            const int64_t base = (first + k) * (COMP ? 2 : 1) * ib + w;
+            const float4 hi = partial[base];
+            const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+            if (COMP) {
+                const float4 lo = partial[base + ib];
+                const float l[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    // TwoSum(S, h) then add the chunk's lost low part (h - l is its value)
+                    const float t = __fadd_rn(S[q], h[q]);
+                    const float bp = __fsub_rn(t, S[q]);
+                    const float e = __fadd_rn(__fsub_rn(S[q], __fsub_rn(t, bp)), __fsub_rn(h[q], bp));
+                    S[q] = t;
+                    E[q] = __fadd_rn(E[q], __fsub_rn(e, l[q]));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) S[q] = __fadd_rn(S[q], h[q]);
+            }
+        }
+        const int64_t gi = o + li;
+        a[3 * gi + 0] = 0.25f * __fadd_rn(S[0], E[0]);
+        a[3 * gi + 1] = 0.25f * __fadd_rn(S[1], E[1]);
+        a[3 * gi + 2] = 0.25f * __fadd_rn(S[2], E[2]);
+        p[gi] = __fadd_rn(S[3], E[3]);
     }
 }
 
@@ -351,9 +436,9 @@ __global__ void batch_kick_kernel(double *__restrict__ v, const float *__restric
 }
 
 // Registry of batched shapes.
-template <int T, int I, int J, int S, bool C>
+template <int W, int I, int J, int S, bool C>
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t st) {
-    batched_pair_kernel<T, I, J, S, C><<<grid, T, smem, st>>>(a);
+    batched_pair_kernel<W, I, J, S, C><<<grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -365,18 +450,19 @@ struct BatchVariant {
     cudaError_t (*launch)(const BatchArgs &, int, size_t, cudaStream_t);
 };
 
-template <int S, int J>
+template <int W, int S, int J>
 constexpr size_t batch_smem() {
-    return (size_t)S * J * sizeof(JPart) + (size_t)S * sizeof(uint64_t) + S * sizeof(StageMeta) +
-           S * sizeof(int);
+    return (size_t)W * S * (J * sizeof(JPart) + sizeof(uint64_t) + sizeof(StageMeta) + sizeof(int));
 }
 
-#define NB_BVARIANT(T, I, J, S, C) \
-    {T, I, J, S, C, (const void *)batched_pair_kernel<T, I, J, S, C>, batch_smem<S, J>(), launch_batched<T, I, J, S, C>}
+// threads = warps x 32; ipt; jtile; stages
+#define NB_BVARIANT(W, I, J, S, C)                                                            \
+    {W * 32, I, J, S, C, (const void *)batched_pair_kernel<W, I, J, S, C>, batch_smem<W, S, J>(), \
+     launch_batched<W, I, J, S, C>}
 
 static const BatchVariant kBatch[] = {
-    NB_BVARIANT(64, 2, 128, 4, false),
-    NB_BVARIANT(64, 2, 128, 4, true),
+    NB_BVARIANT(4, 4, 128, 3, false),
+    NB_BVARIANT(4, 4, 128, 3, true),
 };
 #undef NB_BVARIANT
 
@@ -387,7 +473,14 @@ using namespace nbx;
 
 namespace {
 
-enum BSlot { B_JP = 5, B_POFF = 6, B_ITEMS = 7, B_NITEMS = 8 };
+enum BSlot : int {
+    B_JP = SLOT_BATCH_JP,
+    B_POFF = SLOT_BATCH_POFF,
+    B_ITEMS = SLOT_BATCH_ITEMS,
+    B_NITEMS = SLOT_BATCH_COUNT,
+    B_PART = SLOT_BATCH_PART,
+    B_IBASE = SLOT_BATCH_IBASE
+};
 
 void *bslot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
 
@@ -406,6 +499,8 @@ struct BatchPlanHost {
 };
 
 int batch_resident(const BatchVariant &v, int sm_count) {
+    if (v.smem > 48 * 1024)
+        cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.kernel, v.threads, v.smem) !=
             cudaSuccess ||
@@ -418,19 +513,24 @@ int batch_resident(const BatchVariant &v, int sm_count) {
 // Scratch for a batch, sized from (n_total, C) alone (offsets stay on the device).
 nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, BatchPlanHost *out) {
     const BatchVariant &v = kBatch[comp ? 1 : 0];
-    const int ib = v.threads * v.ipt;
+    const int ib = 32 * v.ipt;  // one warp per work item
     out->v = &v;
     out->n_total = n_total;
     out->cap_padded = n_total + C * (int64_t)kClusterPad;
-    out->cap_items = out->cap_padded / ib + 1;
+    out->cap_items = kMaxChunks * (out->cap_padded / ib) + 1;
     if (out->cap_items > 0x7fffffff || C > 0x7fffffff)
         return fail(ctx, NB_ERR_ARG, "batch too large for 32-bit work items");
     out->grid = batch_resident(v, ctx_sm_count(ctx));
     nb_status st;
     if ((st = bensure(ctx, B_JP, (size_t)out->cap_padded * sizeof(JPart))) != NB_OK) return st;
     if ((st = bensure(ctx, B_POFF, (size_t)(C + 1) * sizeof(int64_t))) != NB_OK) return st;
-    if ((st = bensure(ctx, B_ITEMS, (size_t)out->cap_items * sizeof(int2))) != NB_OK) return st;
+    if ((st = bensure(ctx, B_ITEMS, (size_t)out->cap_items * sizeof(int4))) != NB_OK) return st;
     if ((st = bensure(ctx, B_NITEMS, 2 * sizeof(int))) != NB_OK) return st;  // count, queue head
+    if ((st = bensure(ctx, B_IBASE, (size_t)std::max<int64_t>(C, 1) * sizeof(int64_t))) != NB_OK)
+        return st;
+    if ((st = bensure(ctx, B_PART, (size_t)out->cap_items * ib * sizeof(float4) * (comp ? 2 : 1))) !=
+        NB_OK)
+        return st;
     return NB_OK;
 }
 
@@ -442,9 +542,11 @@ nb_status batch_plan(nb_ctx *ctx, const int64_t *offsets, int64_t C, const Batch
     P.n_total = h.n_total;
     P.cap_padded = h.cap_padded;
     P.cap_items = h.cap_items;
-    P.ib = h.v->threads * h.v->ipt;
+    P.ib = 32 * h.v->ipt;
+    P.jt = h.v->jtile;
     P.poff = static_cast<int64_t *>(bslot(ctx, B_POFF));
-    P.items = static_cast<int2 *>(bslot(ctx, B_ITEMS));
+    P.items = static_cast<int4 *>(bslot(ctx, B_ITEMS));
+    P.ibase = static_cast<int64_t *>(bslot(ctx, B_IBASE));
     P.nitems = static_cast<int *>(bslot(ctx, B_NITEMS));
     P.err = ctx_err_word(ctx);
     batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(P);
@@ -464,11 +566,10 @@ nb_status batch_pair(nb_ctx *ctx, const int64_t *offsets, int64_t C, const float
     A.off = offsets;
     A.poff = static_cast<const int64_t *>(bslot(ctx, B_POFF));
     A.eps = eps;
-    A.items = static_cast<const int2 *>(bslot(ctx, B_ITEMS));
+    A.items = static_cast<const int4 *>(bslot(ctx, B_ITEMS));
     A.nitems = nit;
     A.counter = nit + 1;
-    A.a = a;
-    A.p = p;
+    A.partial = static_cast<float4 *>(bslot(ctx, B_PART));
     A.err = ctx_err_word(ctx);
     A.wait_ns = ctx_wait_ns(ctx);
     {
@@ -476,6 +577,16 @@ nb_status batch_pair(nb_ctx *ctx, const int64_t *offsets, int64_t C, const float
         e = h.v->launch(A, h.grid, h.v->smem, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched pair kernel launch");
+    const int ib = 32 * h.v->ipt;
+    if (h.v->comp)
+        batch_combine_kernel<true><<<(unsigned)C, 256, 0, st>>>(
+            A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), ib,
+            h.v->jtile, a, p);
+    else
+        batch_combine_kernel<false><<<(unsigned)C, 256, 0, st>>>(
+            A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), ib,
+            h.v->jtile, a, p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "batched combine launch");
     return NB_OK;
 }
 

@@ -126,6 +126,8 @@ bool ctx_set_timing(nb_ctx *ctx, bool on) {
 }
 uint64_t ctx_wait_ns(const nb_ctx *ctx) { return ctx->wait_ns; }
 
+static_assert(ExtState::kSlots == SLOT_COUNT, "one buffer per slot id");
+
 cudaError_t ensure_buffer(void **ptr, size_t *cap, size_t bytes) {
     if (bytes <= *cap && *ptr) return cudaSuccess;
     if (*ptr) {

@@ -139,7 +139,14 @@ using namespace nbx;
 
 namespace {
 
-enum Slot { S_JP = 0, S_A = 1, S_P = 2, S_EBLK = 3, S_EOUT = 4, S_PERM = 11 };
+enum Slot : int {
+    S_JP = SLOT_FP64_JP,
+    S_A = SLOT_ENERGY_A,
+    S_P = SLOT_P,
+    S_EBLK = SLOT_ENERGY_BLK,
+    S_EOUT = SLOT_ENERGY_OUT,
+    S_PERM = SLOT_FRAMES
+};
 
 void *slot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
 

@@ -9,9 +9,28 @@
 
 namespace nbx {
 
-// Grow-only device buffers owned by the context for the other entry points.
+// Grow-only device buffers owned by the context for the other entry points,
+// one per slot id (every translation unit takes its ids from this list).
+enum ExtSlot : int {
+    SLOT_FP64_JP = 0,   // packed particles from FP64 state (leap-frog, energy)
+    SLOT_ENERGY_A,      // accelerations computed by nb_energy
+    SLOT_P,             // potentials when the caller passes none
+    SLOT_ENERGY_BLK,    // energy block sums
+    SLOT_ENERGY_OUT,    // energy result
+    SLOT_BATCH_JP,      // padded packed clusters
+    SLOT_BATCH_POFF,    // padded cluster offsets
+    SLOT_BATCH_ITEMS,   // batched work items
+    SLOT_BATCH_COUNT,   // item count and queue head
+    SLOT_BATCH_PART,    // per-item partial sums
+    SLOT_BATCH_IBASE,   // first item of each cluster
+    SLOT_VJP_VP,        // packed VJP records
+    SLOT_VJP_PART,      // VJP partial sums
+    SLOT_FRAMES,        // permutation, ordering scratch, reference points
+    SLOT_COUNT
+};
+
 struct ExtState {
-    static constexpr int kSlots = 12;
+    static constexpr int kSlots = SLOT_COUNT;
     void *buf[kSlots] = {};
     size_t cap[kSlots] = {};
 };

@@ -293,7 +293,7 @@ using namespace nbx;
 namespace {
 
 constexpr int kVThreads = 128, kVIpt = 4, kVJt = 128, kVStages = 3;
-enum VSlot { V_VP = 9, V_PART = 10 };
+enum VSlot : int { V_VP = SLOT_VJP_VP, V_PART = SLOT_VJP_PART };
 
 }  // namespace
 
