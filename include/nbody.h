@@ -163,7 +163,9 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
  * nb_force_batched; a [n_total][3] FP32 device, in (if a_valid) / out;
  * p [n_total] FP32 device, out. One persistent pair launch per step; steps
  * after the first are replayed from a CUDA graph when `stream` is not the
- * legacy default stream. Asynchronous.
+ * legacy default stream. In NB_COMPENSATED mode each cluster's FP64
+ * positions enter the pair kernel as FP32 offsets from the cluster's
+ * centroid (formed in FP64). Asynchronous.
  */
 nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const float *m,
                                    const int64_t *offsets, int64_t n_clusters, int64_t n_total,

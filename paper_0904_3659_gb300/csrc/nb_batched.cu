@@ -143,18 +143,45 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPla
     }
 }
 
-// Pack cluster blockIdx.x (FP32 or FP64 source) into its padded slot.
-template <typename T>
-__global__ void batch_pack_kernel(const T *__restrict__ x, const float *__restrict__ m,
-                                  const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
-                                  JPart *__restrict__ jp) {
+// Pack cluster blockIdx.x (FP32 or FP64 source) into its padded slot. With
+// CENTRE (compensated mode, FP64 state) every particle is stored as the FP32
+// offset from the cluster's centroid, formed in FP64: all pairs of a batch
+// lie inside one cluster, so x_i - x_j is then independent of where the
+// cluster sits (no u |x| loss from rounding far-away positions).
+constexpr int kPackThreads = 256;
+
+template <typename T, bool CENTRE>
+__global__ void __launch_bounds__(kPackThreads) batch_pack_kernel(const T *__restrict__ x,
+                                                                  const float *__restrict__ m,
+                                                                  const int64_t *__restrict__ off,
+                                                                  const int64_t *__restrict__ poff,
+                                                                  JPart *__restrict__ jp) {
     const int64_t c = blockIdx.x;
-    const int64_t o = off[c], nc = off[c + 1] - o, po = poff[c], psz = poff[c + 1] - po;
-    for (int64_t li = threadIdx.x; li < psz; li += blockDim.x) {
+    const int64_t o = off[c], po = poff[c], psz = poff[c + 1] - po;
+    const int64_t nc = psz > 0 ? off[c + 1] - o : 0;
+    double cen[3] = {0.0, 0.0, 0.0};
+    if (CENTRE) {
+        __shared__ double s[3][kPackThreads];
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t li = threadIdx.x; li < nc; li += kPackThreads)
+            for (int k = 0; k < 3; ++k) acc[k] += (double)x[3 * (o + li) + k];
+        for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        for (int w = kPackThreads / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+            __syncthreads();
+        }
+        if (nc > 0)
+            for (int k = 0; k < 3; ++k) cen[k] = s[k][0] / (double)nc;
+    }
+    for (int64_t li = threadIdx.x; li < psz; li += kPackThreads) {
         float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
         if (li < nc) {
             const int64_t i = o + li;
-            const float px = (float)x[3 * i], py = (float)x[3 * i + 1], pz = (float)x[3 * i + 2];
+            const float px = (float)((double)x[3 * i] - cen[0]);
+            const float py = (float)((double)x[3 * i + 1] - cen[1]);
+            const float pz = (float)((double)x[3 * i + 2] - cen[2]);
             const float hm = -0.5f * m[i];
             lo = make_float4(-px, -px, -py, -py);
             hi = make_float4(-pz, -pz, hm, hm);
@@ -613,7 +640,7 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
     BatchPlanHost h{};
     if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
     if ((st = batch_plan(ctx, offsets, n_clusters, h, s)) != NB_OK) return st;
-    batch_pack_kernel<float><<<(unsigned)n_clusters, 256, 0, s>>>(
+    batch_pack_kernel<float, false><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
         x, m, offsets, static_cast<const int64_t *>(bslot(ctx, B_POFF)),
         static_cast<JPart *>(bslot(ctx, B_JP)));
     cudaError_t e = cudaGetLastError();
@@ -643,8 +670,14 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
     const unsigned nb3 = (unsigned)((3 * n_total + 255) / 256);
     cudaError_t e;
 
+    const bool centre = mode == NB_COMPENSATED;
     auto force = [&]() -> nb_status {
-        batch_pack_kernel<double><<<(unsigned)n_clusters, 256, 0, s>>>(x, m, offsets, poff, jp);
+        if (centre)
+            batch_pack_kernel<double, true><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
+                x, m, offsets, poff, jp);
+        else
+            batch_pack_kernel<double, false><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
+                x, m, offsets, poff, jp);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(ctx, le, "batched pack launch");
         return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);

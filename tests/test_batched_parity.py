@@ -159,3 +159,47 @@ def test_batched_leapfrog_matches_single_cluster_calls(nb, ctx):
                             stream)
         nb.nb_synchronize(ctx, stream)
         assert np.abs(xs_t.cpu().numpy() - xb[lo:hi]).max() < 1e-8
+
+
+def test_batched_compensated_fp64_state_far_from_origin(nb, ctx, oracle_mod):
+    # Clusters placed far from the origin (FP64 state): the compensated batch
+    # packs offsets from each cluster's centroid, so its error no longer
+    # depends on where the cluster sits (plain rounding of |x| ~ 1e3 loses
+    # u |x|); what remains is the rounding of the offsets inside the cluster's
+    # own frame, the floor a centred system has (a few 1e-6 at these sizes).
+    import torch
+    dev = torch.device("cuda:0")
+    sizes = [900, 2500, 300]
+    shifts = [np.array([1000.0, 0, 0]), np.array([-500.0, 750.0, 20.0]), np.array([0, 0, 3000.0])]
+    xs, ms = [], []
+    for k, s in enumerate(sizes):
+        x, _, m = workloads.plummer(s, seed=300 + k)
+        xs.append(x + shifts[k])
+        ms.append(m)
+    x64 = np.concatenate(xs)
+    m32 = np.concatenate(ms).astype(np.float32)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    eps32 = np.full(len(sizes), 1.0 / 128, np.float32)
+    n = x64.shape[0]
+    worst = {}
+    for mode in (0, 1):
+        xt = torch.from_numpy(x64.copy()).to(dev)
+        vt = torch.zeros_like(xt)
+        mt = torch.from_numpy(m32).to(dev)
+        ot = torch.from_numpy(offsets).to(dev)
+        et = torch.from_numpy(eps32).to(dev)
+        a = torch.zeros((n, 3), device=dev)
+        p = torch.zeros(n, device=dev)
+        torch.cuda.synchronize()
+        nb.nb_leapfrog_batched_step(ctx, xt, vt, mt, ot, len(sizes), n, et, a, p, 0.0, 0, 0, mode)
+        nb.nb_synchronize(ctx)
+        A, P = a.cpu().numpy().astype(np.float64), p.cpu().numpy().astype(np.float64)
+        w = 0.0
+        for c in range(len(sizes)):
+            lo, hi = offsets[c], offsets[c + 1]
+            ra, rp, ramag = oracle_mod.force(x64[lo:hi], m32[lo:hi], eps32[c])
+            w = max(w, (np.linalg.norm(A[lo:hi] - ra, axis=1) / ramag).max(),
+                    (np.abs(P[lo:hi] - rp) / rp).max())
+        worst[mode] = w
+    assert worst[1] <= 5e-6, worst
+    assert worst[1] * 100 <= worst[0], worst
