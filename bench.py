@@ -641,6 +641,47 @@ def run_case(args):
           flush=True)
 
 
+def run_sweep(args):
+    """Every compiled tile shape of both modes at N = 2^12 .. 2^20: the pair
+    kernel's rate from the library's per-kernel events (one JSON line per
+    shape and size). The tuner's search space, measured."""
+    import torch
+    import paper_0904_3659_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    sizes = [int(v) for v in args.sweep_sizes.split(",")]
+    for n in sizes:
+        x32, m32 = make_inputs(n, 0)
+        x = torch.from_numpy(x32).to(dev)
+        mt = torch.from_numpy(m32).to(dev)
+        a = torch.empty((n, 3), device=dev)
+        p = torch.empty(n, device=dev)
+        reps = 3 if n >= 1 << 19 else (10 if n >= 1 << 16 else 50)
+        for mode, mname in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
+            for t in nb.nb_list_tiles(mode):
+                nb.nb_set_tile(ctx, mode, t)
+                for _ in range(2):
+                    nb.nb_force(ctx, x, mt, n, 1.0 / 256, a, p, mode)
+                nb.nb_synchronize(ctx)
+                nb.nb_timing_enable(ctx, True)
+                nb.nb_timing_reset(ctx)
+                for _ in range(reps):
+                    nb.nb_force(ctx, x, mt, n, 1.0 / 256, a, p, mode)
+                nb.nb_synchronize(ctx)
+                ms, cnt = nb.nb_timing_read(ctx, nb.KERNEL_PAIR)
+                nb.nb_timing_enable(ctx, False)
+                pair_ms = ms / cnt
+                print(json.dumps({"n": n, "mode": mname, "tile": list(t.as_tuple()),
+                                  "pair_ms": pair_ms, "gint_s": n * n / (pair_ms * 1e-3) / 1e9}),
+                      flush=True)
+            nb.nb_set_tile(ctx, mode, None)
+        tuned = {}
+        for mode, mname in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
+            t, rate = nb.nb_autotune(ctx, n, mode)
+            tuned[mname] = {"tile": list(t.as_tuple()), "gint_s_step": rate / 1e9}
+        print(json.dumps({"n": n, "autotune": tuned}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -656,6 +697,9 @@ def main(argv=None):
     ap.add_argument("--tile-comp", default="", help="compensated tile: threads,ipt,jtile,stages")
     ap.add_argument("--plain-only", action="store_true")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--sweep", action="store_true",
+                    help="rate of every compiled tile shape over --sweep-sizes (JSON lines)")
+    ap.add_argument("--sweep-sizes", default="4096,16384,65536,262144,1048576")
     ap.add_argument("--case", choices=["pair", "comp", "batched", "vjp"], default="",
                     help="time one kernel class at a small size (profiler captures)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
@@ -666,6 +710,8 @@ def main(argv=None):
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

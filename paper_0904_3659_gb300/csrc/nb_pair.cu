@@ -469,9 +469,13 @@ const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
     return nullptr;
 }
 
+// Built-in choices per size class, from the measured shape sweep (GB300):
+// short tiles with 2 i per thread while the work cannot fill the GPU with
+// large i-blocks, the 6-8 i per thread shapes from N = 2^15 on.
 int pair_default_index(bool comp, int64_t n) {
-    (void)comp;
-    return n >= (int64_t)1 << 16 ? 0 : 1;
+    if (n >= (int64_t)1 << 15) return 0;
+    if (comp) return n >= (int64_t)1 << 13 ? 1 : 8;   // (64,2,64,4) / (128,2,128,4)
+    return n >= (int64_t)1 << 13 ? 10 : 9;            // (128,2,128,4) / (256,2,128,4)
 }
 
 PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
