@@ -252,6 +252,11 @@ nb_status nb_get_tile(nb_ctx *ctx, int64_t n, nb_mode mode, nb_tile *out);
  * nb_list_tiles); NULL clears the override. */
 nb_status nb_set_tile(nb_ctx *ctx, nb_mode mode, const nb_tile *tile);
 
+/* Record `tile` (one of the compiled shapes) as the tuned shape for n's size
+ * class (floor(log2 n)) in `mode`, as nb_autotune does after timing; NULL
+ * forgets that class's entry. Used to restore saved tuning results. */
+nb_status nb_set_tuned_tile(nb_ctx *ctx, int64_t n, nb_mode mode, const nb_tile *tile);
+
 /* The compiled tile shapes of `mode`. Writes up to `cap` entries to out (may
  * be NULL) and the total count to *count. */
 nb_status nb_list_tiles(nb_mode mode, nb_tile *out, int cap, int *count);

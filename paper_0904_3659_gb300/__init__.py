@@ -25,7 +25,8 @@ __all__ = [
     "library", "library_path", "exported_symbols", "Context",
     "nb_create", "nb_destroy", "nb_last_error", "nb_status_string", "nb_force",
     "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_batched_step", "nb_leapfrog_step", "nb_energy",
-    "nb_force_vjp", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_list_tiles",
+    "nb_force_vjp", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_set_tuned_tile", "nb_list_tiles",
+    "tune_to_file", "load_tuning",
     "nb_autotune", "nb_timing_enable", "nb_timing_read", "nb_timing_reset",
     "nb_debug_set_fault", "nb_force_noalloc", "force",
 ]
@@ -91,6 +92,7 @@ _SIGNATURES = {
     "nb_synchronize": (_c.c_int, [_P, _P]),
     "nb_get_tile": (_c.c_int, [_P, _I64, _c.c_int, _c.POINTER(nb_tile)]),
     "nb_set_tile": (_c.c_int, [_P, _c.c_int, _c.POINTER(nb_tile)]),
+    "nb_set_tuned_tile": (_c.c_int, [_P, _I64, _c.c_int, _c.POINTER(nb_tile)]),
     "nb_list_tiles": (_c.c_int, [_c.c_int, _c.POINTER(nb_tile), _c.c_int, _c.POINTER(_c.c_int)]),
     "nb_autotune": (_c.c_int, [_P, _I64, _c.c_int, _P, _c.POINTER(nb_tile),
                                _c.POINTER(_c.c_double)]),
@@ -267,6 +269,52 @@ def nb_set_tile(ctx, mode, tile) -> None:
     if not isinstance(tile, nb_tile):
         tile = nb_tile(*tile)
     _check(ctx, library().nb_set_tile(ctx.handle, int(mode), ctypes.byref(tile)))
+
+
+def nb_set_tuned_tile(ctx, n, mode, tile) -> None:
+    if tile is None:
+        _check(ctx, library().nb_set_tuned_tile(ctx.handle, int(n), int(mode), None))
+        return
+    if not isinstance(tile, nb_tile):
+        tile = nb_tile(*tile)
+    _check(ctx, library().nb_set_tuned_tile(ctx.handle, int(n), int(mode), ctypes.byref(tile)))
+
+
+def tune_to_file(ctx, sizes, path, modes=(NB_PLAIN, NB_COMPENSATED)):
+    """Run nb_autotune for every size and mode and save the picks as JSON
+    ({"device": ..., "entries": [{"mode", "n", "tile", "rate"}]})."""
+    import json
+    entries = []
+    for mode in modes:
+        for n in sizes:
+            t, rate = nb_autotune(ctx, n, mode)
+            entries.append({"mode": int(mode), "n": int(n), "tile": list(t.as_tuple()),
+                            "rate": rate})
+    device = None
+    try:
+        import torch
+        device = torch.cuda.get_device_name(ctx.device)
+    except Exception:
+        pass
+    with open(path, "w") as f:
+        json.dump({"device": device, "entries": entries}, f, indent=1)
+    return entries
+
+
+def load_tuning(ctx, path) -> int:
+    """Restore tuning picks saved by tune_to_file; returns how many applied
+    (entries naming a shape this build does not compile are skipped)."""
+    import json
+    with open(path) as f:
+        data = json.load(f)
+    applied = 0
+    for e in data.get("entries", []):
+        try:
+            nb_set_tuned_tile(ctx, e["n"], e["mode"], tuple(e["tile"]))
+            applied += 1
+        except NBError:
+            pass
+    return applied
 
 
 def nb_list_tiles(mode=NB_PLAIN) -> list:

@@ -480,6 +480,24 @@ nb_status nb_set_tile(nb_ctx *ctx, nb_mode mode, const nb_tile *tile) {
     return fail(ctx, NB_ERR_ARG, "tile shape is not one of the compiled shapes");
 }
 
+nb_status nb_set_tuned_tile(nb_ctx *ctx, int64_t n, nb_mode mode, const nb_tile *tile) {
+    if (!ctx) return NB_ERR_ARG;
+    if (n <= 0) return fail(ctx, NB_ERR_ARG, "n must be > 0");
+    if (mode != NB_PLAIN && mode != NB_COMPENSATED) return fail(ctx, NB_ERR_ARG, "unknown mode");
+    const bool comp = mode == NB_COMPENSATED;
+    const int mi = comp ? 1 : 0;
+    if (!tile) {
+        ctx->tuned[mi].erase(size_class(n));
+        return NB_OK;
+    }
+    for (int k = 0; k < pair_variant_count(comp); ++k)
+        if (same_tile(pair_variant(comp, k)->tile, *tile)) {
+            ctx->tuned[mi][size_class(n)] = k;
+            return NB_OK;
+        }
+    return fail(ctx, NB_ERR_ARG, "tile shape is not one of the compiled shapes");
+}
+
 nb_status nb_list_tiles(nb_mode mode, nb_tile *out, int cap, int *count) {
     if (!count) return NB_ERR_ARG;
     if (mode != NB_PLAIN && mode != NB_COMPENSATED) return NB_ERR_ARG;

@@ -246,3 +246,17 @@ def test_force_host_matches_device(nb, ctx):
     nb.nb_force_host(ctx, x32.ctypes.data, m32.ctypes.data, 5000, np.float32(0.01),
                      a.ctypes.data, p.ctypes.data, 0)
     assert a.tobytes() == a_dev.tobytes() and p.tobytes() == p_dev.tobytes()
+
+
+def test_tuning_saved_and_restored(nb, ctx, tmp_path):
+    # nb_autotune's picks survive a new context through the JSON file.
+    path = tmp_path / "tuning.json"
+    entries = nb.tune_to_file(ctx, [3000], str(path), modes=(0,))
+    fresh = nb.Context(0)
+    try:
+        assert nb.load_tuning(fresh, str(path)) == 1
+        assert nb.nb_get_tile(fresh, 3000, 0).as_tuple() == tuple(entries[0]["tile"])
+        nb.nb_set_tuned_tile(fresh, 3000, 0, None)
+        assert nb.nb_get_tile(fresh, 3000, 0).as_tuple() == nb.nb_get_tile(nb.Context(0), 3000, 0).as_tuple()
+    finally:
+        fresh.close()
