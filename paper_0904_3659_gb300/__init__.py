@@ -44,7 +44,9 @@ NB_COMPENSATED = 1
 KERNEL_PACK, KERNEL_PAIR, KERNEL_REDUCE, KERNEL_LEAPFROG, KERNEL_BATCHED, KERNEL_VJP = range(6)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-library_path = os.path.join(_HERE, "libnbody.so")
+# NB_LIBRARY selects another build of the library (e.g. libnbody_debug.so,
+# the bounds-checked build); the default is the in-tree release build.
+library_path = os.environ.get("NB_LIBRARY") or os.path.join(_HERE, "libnbody.so")
 
 
 class nb_tile(ctypes.Structure):

@@ -4,7 +4,12 @@ Each csrc/*.cu is compiled to an object under _build/ in parallel, then the
 objects are linked into paper_0904_3659_gb300/libnbody.so (CUDA runtime
 linked statically, so the library loads without a GPU present).
 
-    python -m paper_0904_3659_gb300.build [--force] [--verbose]
+With debug=True the same sources are compiled with -DNB_DEBUG into
+_build_debug/ and libnbody_debug.so: every computed-index access in the
+kernels is checked against its buffer's extent, and a violation is recorded
+in the context's error word (reported by nb_synchronize) and skipped.
+
+    python -m paper_0904_3659_gb300.build [--force] [--verbose] [--debug]
 """
 from __future__ import annotations
 
@@ -20,6 +25,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnbody.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libnbody_debug.so")
 HEADERS = [os.path.join(ROOT, "include", "nbody.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -35,17 +42,20 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          debug: bool = False) -> str:
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    extra = ["-DNB_DEBUG"] if debug else []
+    os.makedirs(build_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + HEADERS
     jobs = []
     objs = []
     for src in sources:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src, *headers]):
-            cmd = [NVCC, *ARCH, *CFLAGS, "-c", src, "-o", obj]
+            cmd = [NVCC, *ARCH, *CFLAGS, *extra, "-c", src, "-o", obj]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
@@ -67,14 +77,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if failed:
         msg = "\n".join(f"$ {' '.join(c)}\n{e}" for c, e in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
@@ -82,5 +92,6 @@ if __name__ == "__main__":
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--ptxas-info", action="store_true")
+    ap.add_argument("--debug", action="store_true")
     a = ap.parse_args()
-    print(build(force=a.force, verbose=a.verbose, ptxas_info=a.ptxas_info))
+    print(build(force=a.force, verbose=a.verbose, ptxas_info=a.ptxas_info, debug=a.debug))

@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(kPackThreads) batch_pack_kernel(const T *__res
     }
 }
 
+
 struct BatchArgs {
     const JPart *jp;
     const int64_t *off;
@@ -203,6 +204,7 @@ struct BatchArgs {
     float4 *partial;  // [item][words][ib]: one item's sums for its i-block
     int *err;
     uint64_t wait_ns;
+    int64_t cap_padded, cap_items, partial_len;  // extents (debug-build bounds checks)
 };
 
 struct StageMeta {
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
         const int s = kk % STAGES;
         if (!p_done && p_jt >= p_ntiles) {
             const int it = atomicAdd(A.counter, 1);
-            if (it >= nitems) {
+            if (it >= nitems || !NB_IN(A.err, 10, it < A.cap_items)) {
                 p_done = 1;
             } else {
                 const int4 w = A.items[it];
@@ -274,7 +276,11 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
         mt.iblock = p_b;
         mt.jt = p_jt;
         meta[s] = mt;
+        if (!p_done && !NB_IN(A.err, 11, p_base + (int64_t)(p_jt + 1) * JT <= A.cap_padded))
+            p_done = 1;
         if (p_done) {
+            mt.end = 1;
+            meta[s] = mt;
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s]))
                          : "memory");
         } else {
@@ -295,6 +301,7 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
 
     // The item's sums (and Kahan carries) for its i-block.
     auto write_out = [&]() {
+        if (!NB_IN(A.err, 13, ((int64_t)cur_item + 1) * (COMP ? 2 : 1) * IB <= A.partial_len)) return;
         float4 *dst = A.partial + (int64_t)cur_item * (COMP ? 2 : 1) * IB;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
@@ -330,7 +337,8 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
             const int64_t base = A.poff[cur_cluster] + (int64_t)cur_b * IB;
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                const int64_t i0 = base + (2 * q) * 32 + lane, i1 = i0 + 32;
+                int64_t i0 = base + (2 * q) * 32 + lane, i1 = i0 + 32;
+                if (!NB_IN(A.err, 12, i1 < A.cap_padded)) i0 = i1 = 0;
                 const float4 A0 = reinterpret_cast<const float4 *>(A.jp + i0)[0];
                 const float4 B0 = reinterpret_cast<const float4 *>(A.jp + i0)[1];
                 const float4 A1 = reinterpret_cast<const float4 *>(A.jp + i1)[0];
@@ -397,7 +405,8 @@ template <bool COMP>
 __global__ void batch_combine_kernel(const float4 *__restrict__ partial,
                                      const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
                                      const int64_t *__restrict__ ibase, int ib, int jt,
-                                     float *__restrict__ a, float *__restrict__ p) {
+                                     float *__restrict__ a, float *__restrict__ p,
+                                     int64_t partial_len, int64_t n_total, int *err) {
     const int64_t c = blockIdx.x;
     // poff holds the validated padded sizes: all zero when the planner
     // rejected the offsets, so nothing is written for an invalid batch, and
@@ -414,6 +423,7 @@ __global__ void batch_combine_kernel(const float4 *__restrict__ partial,
         float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
         for (int64_t k = 0; k < nch; ++k) {
             const int64_t base = (first + k) * (COMP ? 2 : 1) * ib + w;
+            if (!NB_IN(err, 14, base + (COMP ? ib : 0) < partial_len)) continue;
             const float4 hi = partial[base];
             const float h[4] = {hi.x, hi.y, hi.z, hi.w};
             if (COMP) {
@@ -434,6 +444,7 @@ __global__ void batch_combine_kernel(const float4 *__restrict__ partial,
             }
         }
         const int64_t gi = o + li;
+        if (!NB_IN(err, 14, gi >= 0 && gi < n_total)) continue;
         a[3 * gi + 0] = 0.25f * __fadd_rn(S[0], E[0]);
         a[3 * gi + 1] = 0.25f * __fadd_rn(S[1], E[1]);
         a[3 * gi + 2] = 0.25f * __fadd_rn(S[2], E[2]);
@@ -599,6 +610,9 @@ nb_status batch_pair(nb_ctx *ctx, const int64_t *offsets, int64_t C, const float
     A.partial = static_cast<float4 *>(bslot(ctx, B_PART));
     A.err = ctx_err_word(ctx);
     A.wait_ns = ctx_wait_ns(ctx);
+    A.cap_padded = h.cap_padded;
+    A.cap_items = h.cap_items;
+    A.partial_len = h.cap_items * (int64_t)(32 * h.v->ipt) * (h.v->comp ? 2 : 1);
     {
         TimedLaunch t(ctx, 4, st);
         e = h.v->launch(A, h.grid, h.v->smem, st);
@@ -608,11 +622,11 @@ nb_status batch_pair(nb_ctx *ctx, const int64_t *offsets, int64_t C, const float
     if (h.v->comp)
         batch_combine_kernel<true><<<(unsigned)C, 256, 0, st>>>(
             A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), ib,
-            h.v->jtile, a, p);
+            h.v->jtile, a, p, A.partial_len, h.n_total, A.err);
     else
         batch_combine_kernel<false><<<(unsigned)C, 256, 0, st>>>(
             A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), ib,
-            h.v->jtile, a, p);
+            h.v->jtile, a, p, A.partial_len, h.n_total, A.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "batched combine launch");
     return NB_OK;
 }

@@ -202,6 +202,8 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     pa.eps2 = eps * eps;
     pa.fault_unit = ctx->fault_unit;
     pa.wait_ns = ctx->wait_ns;
+    pa.npad = plan.npad;
+    pa.partial_len = (int64_t)(ctx->partial_bytes / sizeof(float4));
     {
         TimedLaunch t(ctx, K_PAIR, st);
         e = v.launch(pa, plan.grid, v.smem, st);
@@ -218,6 +220,8 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     ra.grid = plan.grid;
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
+    ra.partial_len = pa.partial_len;
+    ra.err = ctx->d_err;
     {
         TimedLaunch t(ctx, K_REDUCE, st);
         e = launch_reduce(ra, comp, st);
@@ -252,6 +256,8 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
     pa.fault_unit = ctx->fault_unit;
     pa.wait_ns = ctx->wait_ns;
     pa.cref = cref;
+    pa.npad = plan.npad;
+    pa.partial_len = (int64_t)(ctx->partial_bytes / sizeof(float4));
     cudaError_t e;
     {
         TimedLaunch t(ctx, K_PAIR, st);
@@ -269,6 +275,8 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
     ra.perm = perm;
+    ra.partial_len = pa.partial_len;
+    ra.err = ctx->d_err;
     {
         TimedLaunch t(ctx, K_REDUCE, st);
         e = launch_reduce(ra, true, st);
@@ -445,6 +453,10 @@ nb_status nb_synchronize(nb_ctx *ctx, void *stream) {
         if (word & nbdev::kErrTimeout)
             return fail(ctx, NB_ERR_TIMEOUT,
                         "a bounded wait for a shared-memory tile ran out; results are invalid");
+        if (word & nbdev::kErrBounds)
+            return fail(ctx, NB_ERR_CUDA,
+                        "debug bounds check failed at site " + std::to_string((word >> 8) & 0xff) +
+                            "; the access was skipped and results are invalid");
         if (word & nbdev::kErrBatchPlan)
             return fail(ctx, NB_ERR_ARG,
                         "batched offsets are invalid (they must start at 0, never decrease and "

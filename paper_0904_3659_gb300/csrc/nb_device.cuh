@@ -11,6 +11,7 @@ namespace nbdev {
 // Error bits a kernel records in the context's device error word.
 constexpr int kErrTimeout = 1;
 constexpr int kErrBatchPlan = 2;  // batched offsets exceed the capacity sized from n_total
+constexpr int kErrBounds = 4;     // a checked access was out of range (debug builds)
 
 // Default limit for one bounded wait on a shared-memory barrier.
 constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // one second
@@ -78,6 +79,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
     return false;
 }
+
+// Bounds checks of the debug build (-DNB_DEBUG, libnbody_debug.so). NB_IN(err,
+// site, cond) is true when the access it guards may go ahead; in a debug
+// build a false cond records kErrBounds and the check site (bits 8..15) in
+// the error word, and the caller skips the access. Release builds compile
+// the check away.
+#ifdef NB_DEBUG
+__device__ __forceinline__ bool nb_in(int *err, int site, bool cond) {
+    if (!cond) atomicOr(err, kErrBounds | (site << 8));
+    return cond;
+}
+#define NB_IN(err, site, cond) ::nbdev::nb_in((err), (site), (cond))
+#else
+#define NB_IN(err, site, cond) true
+#endif
 
 // Reciprocal square root on the special-function unit (approximate; one
 // Newton-Raphson step is applied by the caller).

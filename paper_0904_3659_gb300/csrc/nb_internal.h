@@ -40,6 +40,8 @@ struct PairArgs {
     int64_t fault_unit;    // test hook: unit whose copy is never issued (-1: none)
     uint64_t wait_ns;      // limit of one bounded barrier wait
     const float4 *cref;    // per-j-tile reference points (frame variants only)
+    int64_t npad;          // entries of jp (bounds checks of the debug build)
+    int64_t partial_len;   // float4 entries of partial (debug build)
 };
 
 // Arguments of the deterministic cross-CTA combine.
@@ -54,6 +56,8 @@ struct ReduceArgs {
     int maxseg;
     int ib;
     const int32_t *perm;   // if set, result k is written to particle perm[k]
+    int64_t partial_len;   // float4 entries of partial (debug build)
+    int *err;              // device error word (debug build)
 };
 
 inline bool same_tile(const nb_tile &a, const nb_tile &b) {
@@ -91,6 +95,7 @@ struct PairPlan {
     int64_t n, npad, nib, njt, units;
     int grid, maxseg, ib, words;
     size_t partial_bytes;
+    int64_t partial_len() const { return (int64_t)(partial_bytes / sizeof(float4)); }
 };
 PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas);
 

@@ -129,6 +129,8 @@ extern "C" nb_status nb_force_noalloc(const float *x, const float *m, int64_t n,
     pa.eps2 = eps * eps;
     pa.fault_unit = -1;
     pa.wait_ns = nbdev::kDefaultWaitNs;
+    pa.npad = plan.npad;
+    pa.partial_len = (int64_t)(plan.partial_bytes / sizeof(float4));
     e = v.launch(pa, plan.grid, v.smem, st);
     if (e != cudaSuccess) return noalloc_fail(NB_ERR_CUDA, cudaGetErrorString(e));
 
@@ -142,6 +144,8 @@ extern "C" nb_status nb_force_noalloc(const float *x, const float *m, int64_t n,
     ra.grid = plan.grid;
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
+    ra.partial_len = pa.partial_len;
+    ra.err = ds.err;
     e = launch_reduce(ra, false, st);
     if (e != cudaSuccess) return noalloc_fail(NB_ERR_CUDA, cudaGetErrorString(e));
 

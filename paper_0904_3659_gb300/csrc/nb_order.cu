@@ -176,7 +176,13 @@ __global__ void __launch_bounds__(JT) frames_pack_kernel(const double *__restric
     const int t = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * JT + t;
     const bool real = k < n;
-    const int64_t src = real ? perm[k] : 0;
+    int64_t src = real ? perm[k] : 0;
+#ifdef NB_DEBUG
+    // perm must be a permutation of [0, n); checked without an error word
+    // here: an out-of-range entry is replaced by 0 and the particle made inert.
+    const bool ok = src >= 0 && src < n;
+    if (real && !ok) src = 0;
+#endif
     double p[3] = {0.0, 0.0, 0.0};
     if (real)
         for (int c = 0; c < 3; ++c) p[c] = x[3 * src + c];

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
         const int64_t u = u0 + kk;
         if (u == args.fault_unit) return;  // test hook: this copy never happens
         const int64_t jt = u % args.njt;
+        if (!NB_IN(args.err, 2, (jt + 1) * JT <= args.npad)) return;
         issued_at[s] = kk;
         mbar_arrive_expect_tx(&full[s], TILE_BYTES);
         bulk_g2s(tiles + (size_t)s * JT, args.jp + jt * JT, TILE_BYTES, &full[s]);
@@ -158,7 +159,11 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
 
     auto flush = [&](int64_t b) {
         const int64_t seg = b - bfirst;
-        float4 *dst = args.partial + (c * args.maxseg + seg) * (COMP ? 2 : 1) * (int64_t)IB;
+        const int64_t off = (c * args.maxseg + seg) * (COMP ? 2 : 1) * (int64_t)IB;
+        if (!NB_IN(args.err, 3, seg >= 0 && seg < args.maxseg &&
+                                    off + (COMP ? 2 : 1) * IB <= args.partial_len))
+            return;
+        float4 *dst = args.partial + off;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int i0 = (2 * q) * THREADS + tid, i1 = i0 + THREADS;
@@ -193,7 +198,8 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
             cur_b = b;
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                const int64_t i0 = b * IB + (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+                int64_t i0 = b * IB + (2 * q) * THREADS + tid, i1 = i0 + THREADS;
+                if (!NB_IN(args.err, 1, i1 < args.npad)) i0 = i1 = 0;
                 const float4 A0 = reinterpret_cast<const float4 *>(args.jp + i0)[0];
                 const float4 B0 = reinterpret_cast<const float4 *>(args.jp + i0)[1];
                 const float4 A1 = reinterpret_cast<const float4 *>(args.jp + i1)[0];
@@ -238,7 +244,8 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
             zr[q] = zi[q];
         }
         if (FR) {
-            const float4 cj = args.cref[jt];
+            const float4 cj = NB_IN(args.err, 4, (jt + 1) * JT <= args.npad) ? args.cref[jt]
+                                                                             : make_float4(0, 0, 0, 0);
             const float2 ncx = splat2(-cj.x), ncy = splat2(-cj.y), ncz = splat2(-cj.z);
 #pragma unroll
             for (int q = 0; q < P; ++q) {
@@ -328,13 +335,16 @@ __global__ void reduce_plain_kernel(const ReduceArgs r) {
     float ax = 0.f, ay = 0.f, az = 0.f, pp = 0.f;
     for (int64_t c = clo; c <= chi; ++c) {
         const int64_t bf = (c * r.units / r.grid) / r.njt;
-        const float4 v = r.partial[(c * r.maxseg + (b - bf)) * r.ib + w];
+        const int64_t idx = (c * r.maxseg + (b - bf)) * r.ib + w;
+        if (!NB_IN(r.err, 5, b - bf >= 0 && b - bf < r.maxseg && idx < r.partial_len)) continue;
+        const float4 v = r.partial[idx];
         ax = __fadd_rn(ax, v.x);
         ay = __fadd_rn(ay, v.y);
         az = __fadd_rn(az, v.z);
         pp = __fadd_rn(pp, v.w);
     }
     const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
+    if (!NB_IN(r.err, 6, o >= 0 && o < r.n)) return;
     r.a[3 * o + 0] = 0.25f * ax;
     r.a[3 * o + 1] = 0.25f * ay;
     r.a[3 * o + 2] = 0.25f * az;
@@ -359,6 +369,8 @@ __global__ void reduce_comp_kernel(const ReduceArgs r) {
     for (int64_t c = clo; c <= chi; ++c) {
         const int64_t bf = (c * r.units / r.grid) / r.njt;
         const int64_t base = (c * r.maxseg + (b - bf)) * 2 * r.ib + w;
+        if (!NB_IN(r.err, 5, b - bf >= 0 && b - bf < r.maxseg && base + r.ib < r.partial_len))
+            continue;
         const float4 hi = r.partial[base];
         const float4 lo = r.partial[base + r.ib];
         const float h[4] = {hi.x, hi.y, hi.z, hi.w};
@@ -372,6 +384,7 @@ __global__ void reduce_comp_kernel(const ReduceArgs r) {
         }
     }
     const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
+    if (!NB_IN(r.err, 6, o >= 0 && o < r.n)) return;
     r.a[3 * o + 0] = 0.25f * __fadd_rn(S[0], E[0]);
     r.a[3 * o + 1] = 0.25f * __fadd_rn(S[1], E[1]);
     r.a[3 * o + 2] = 0.25f * __fadd_rn(S[2], E[2]);

@@ -67,6 +67,7 @@ struct VjpArgs {
     int grid, maxseg;
     float eps2;
     uint64_t wait_ns;
+    int64_t npad, partial_len;  // extents (debug-build bounds checks)
 };
 
 template <int P, int JT, int UNR, bool DIAG>
@@ -148,6 +149,10 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
     auto issue_next = [&]() {
         const int s = issued % STAGES;
         const int64_t jt = (u0 + issued) % args.njt;
+        if (!NB_IN(args.err, 21, (jt + 1) * JT <= args.npad)) {
+            ++issued;
+            return;
+        }
         mbar_arrive_expect_tx(&full[s], TILE_BYTES);
         bulk_g2s(tiles + (size_t)s * JT, args.vp + jt * JT, TILE_BYTES, &full[s]);
         ++issued;
@@ -161,7 +166,9 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
     const float2 zero2 = splat2(0.f);
 
     auto flush = [&](int64_t b) {
-        float4 *dst = args.partial + (c * args.maxseg + (b - bfirst)) * 2 * (int64_t)IB;
+        const int64_t off = (c * args.maxseg + (b - bfirst)) * 2 * (int64_t)IB;
+        if (!NB_IN(args.err, 22, b - bfirst < args.maxseg && off + 2 * IB <= args.partial_len)) return;
+        float4 *dst = args.partial + off;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int i0 = (2 * q) * THREADS + tid, i1 = i0 + THREADS;
@@ -187,7 +194,8 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
                 float e[2][9];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int64_t i = b * IB + (2 * q + h) * THREADS + tid;
+                    int64_t i = b * IB + (2 * q + h) * THREADS + tid;
+                    if (!NB_IN(args.err, 20, i < args.npad)) i = 0;
                     const VPart &V = args.vp[i];
                     e[h][0] = -V.nx.x;
                     e[h][1] = -V.ny.x;
@@ -269,6 +277,7 @@ __global__ void vjp_combine_kernel(const VjpArgs A, int ib, float *__restrict__ 
     for (int64_t c = clo; c <= chi; ++c) {
         const int64_t bf = (c * A.units / A.grid) / A.njt;
         const int64_t base = (c * A.maxseg + (b - bf)) * 2 * ib + w;
+        if (!NB_IN(A.err, 23, b - bf < A.maxseg && base + ib < A.partial_len)) continue;
         const float4 p0 = A.partial[base], p1 = A.partial[base + ib];
         const float v[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
@@ -345,6 +354,8 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
     A.maxseg = plan.maxseg;
     A.eps2 = eps * eps;
     A.wait_ns = ctx_wait_ns(ctx);
+    A.npad = plan.npad;
+    A.partial_len = (int64_t)(es.cap[V_PART] / sizeof(float4));
     {
         TimedLaunch t(ctx, 5, s);
         kernel<<<plan.grid, kVThreads, smem, s>>>(A);
