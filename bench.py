@@ -39,17 +39,30 @@ import workloads  # noqa: E402
 
 WORKLOAD = "plummer1m"
 FLOP_PER_INT_PAPER = 38          # the paper's convention (Section "Experiments")
-FP32_OPS_PER_INT = 16            # FP32 pipe operations per interaction in our kernel
 FP32_LANES_PER_SM = 128          # FP32 lanes per SM per clock
 MUFU_PER_INT = 1
+# The Newton-step tile of the same shape as the default, timed beside it.
+NEWTON_TILE = (128, 8, 256, 3, 8, 1, 1, 0, 63, 1)
+
+
+def fp32_ops_per_interaction(tile) -> int:
+    """FP32 pipe operations per interaction of a pair-kernel tile: 13 with the
+    special-function unit's rsqrt used as is, 16 with one Newton step."""
+    return 16 if tile[9] else 13
+
+
+def alu_peak(sm_count, sm_mhz, ops) -> float:
+    """Interactions per second with every FP32 lane busy (G-int/s)."""
+    return sm_count * sm_mhz * 1e6 * FP32_LANES_PER_SM / ops / 1e9
+
 
 # DRAM bytes (read + write) of one launch of the plain pair kernel, from the
 # ncu capture summarised in profiles/pair_kernel_plain_plummer131072.md
-# (4.224 MB read, 0 written at N = 131072). The kernel reads each j-tile from
+# (4.257 MB read, 0 written at N = 131072). The kernel reads each j-tile from
 # L2 after its first touch, so DRAM traffic grows with N, not N^2; the bench
 # reports it scaled to its N, and null for any other tile shape.
-PROFILED_TILE = (128, 8, 256, 3, 8, 1, 1, 0, 63)
-PROFILED_DRAM_BYTES, PROFILED_N = 4.224e6, 131072
+PROFILED_TILE = (128, 12, 256, 3, 4, 1, 0, 1, 63, 0)
+PROFILED_DRAM_BYTES, PROFILED_N = 4.257e6, 131072
 
 
 # --------------------------------------------------------------------------
@@ -374,21 +387,22 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # Tile choice: tune on a quarter-size proxy (same inner loop; the
-    # persistent split balances the full size), then fix it.
+    # persistent split balances the full size), then record it for N's size
+    # class only (the other workloads keep the shapes of their own sizes).
     tiles = {}
     for mode in ((nb.NB_PLAIN,) if args.plain_only else (nb.NB_PLAIN, nb.NB_COMPENSATED)):
         fixed = args.tile if mode == nb.NB_PLAIN else args.tile_comp
         if fixed:
-            nb.nb_set_tile(ctx, mode, tuple(int(v) for v in fixed.split(",")))
+            nb.nb_set_tuned_tile(ctx, n, mode, tuple(int(v) for v in fixed.split(",")))
         elif args.tile_tune:
             t, _ = nb.nb_autotune(ctx, max(n // 4, 1024), mode)
-            nb.nb_set_tile(ctx, mode, t)
+            nb.nb_set_tuned_tile(ctx, n, mode, t)
         tiles[mode] = nb.nb_get_tile(ctx, n, mode)
         nb.nb_reserve(ctx, n, mode)
 
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
-    def timed(mode, steps, warmup):
+    def timed(mode, steps, warmup, n=n, xt=xt, mt=mt, a=a, p=p):
         for _ in range(warmup):
             nb.nb_force(ctx, xt, mt, n, eps, a, p, mode, stream)
         nb.nb_synchronize(ctx, stream)
@@ -424,6 +438,13 @@ def run_ours(args):
             comp_ms, comp_k = timed(nb.NB_COMPENSATED, args.steps, args.warmup)
             a_comp = a.cpu().numpy()
             p_comp = p.cpu().numpy()
+        newton = None
+        if args.newton_arm and tuple(tiles[nb.NB_PLAIN].as_tuple()) != NEWTON_TILE:
+            # The same work with the Newton step on the reciprocal square root.
+            nb.nb_set_tile(ctx, nb.NB_PLAIN, NEWTON_TILE)
+            newton_ms, newton_k = timed(nb.NB_PLAIN, args.steps, args.warmup)
+            newton = (newton_ms, newton_k, a.cpu().numpy(), p.cpu().numpy())
+            nb.nb_set_tile(ctx, nb.NB_PLAIN, None)
     clocks = clk.summary()
 
     ms_plain = max_over_ranks(sum(plain_ms) / len(plain_ms), world)
@@ -458,8 +479,9 @@ def run_ours(args):
     pair_ms_total, pair_launches = plain_k["pair"]
     pair_ms = pair_ms_total / max(pair_launches, 1)
     achieved = interactions / (pair_ms * 1e-3) / 1e9                     # G-int/s
-    peak = sm_count * sm_max_mhz * 1e6 * FP32_LANES_PER_SM / FP32_OPS_PER_INT / 1e9
-    peak17 = sm_count * sm_max_mhz * 1e6 * FP32_LANES_PER_SM / 17 / 1e9
+    plain_tile = tuple(tiles[nb.NB_PLAIN].as_tuple())
+    ops = fp32_ops_per_interaction(plain_tile)
+    peak = alu_peak(sm_count, sm_max_mhz, ops)
     comp_pair_ms = comp_k["pair"][0] / max(comp_k["pair"][1], 1)
 
     if rank != 0:
@@ -496,19 +518,30 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G-int/s",
                      "frac": achieved / peak,
                      "traffic": (PROFILED_DRAM_BYTES * n / PROFILED_N
-                                 if tuple(tiles[nb.NB_PLAIN].as_tuple()) == PROFILED_TILE else None),
+                                 if plain_tile == PROFILED_TILE else None),
                      "traffic_note": "DRAM bytes per launch, ncu capture at N=131072 scaled by N",
                      "basis": (f"{sm_count} SMs x {sm_max_mhz:.0f} MHz x {FP32_LANES_PER_SM} FP32 "
-                               f"lanes / {FP32_OPS_PER_INT} FP32 ops per interaction "
+                               f"lanes / {ops} FP32 ops per interaction "
                                f"(+{MUFU_PER_INT} MUFU rsqrt, not binding); sm_max_mhz of "
                                f"{'measured' if peaks else 'nvidia-smi'} peaks"),
-                     "frac_17op_convention": achieved / peak17},
+                     "fp32_ops_per_interaction": ops},
         "e2e": ({"value": interactions * world / (e2e_ms_max * 1e-3) / 1e9, "unit": "G-int/s",
                  "h2d_bytes_per_step": int(x32.nbytes + m32.nbytes),
                  "d2h_bytes_per_step": int(4 * n * 3 + 4 * n)} if e2e_ms else None),
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    if newton is not None:
+        newton_ms, newton_k = newton[0], newton[1]
+        n_ms = max_over_ranks(sum(newton_ms) / len(newton_ms), world)
+        n_pair_ms = newton_k["pair"][0] / max(newton_k["pair"][1], 1)
+        n_achieved = interactions / (n_pair_ms * 1e-3) / 1e9
+        n_peak = alu_peak(sm_count, sm_max_mhz, 16)
+        out["newton_step"] = {"tile": list(NEWTON_TILE), "value": aggregate(interactions, world, n_ms) / 1e9,
+                              "unit": "G-int/s", "ms_per_step": n_ms, "pair_ms": n_pair_ms,
+                              "roofline_frac": n_achieved / n_peak, "roofline_peak": n_peak,
+                              "fp32_ops_per_interaction": 16,
+                              "speedup_without_step": n_ms / ms_plain}
     if args.extras:
         plain_rate = value / world / 1e9
         for key, fn in (("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch)),
@@ -529,6 +562,8 @@ def run_ours(args):
         out["oracle_error"] = {"rows": int(rows.size),
                                "plain": oracle_errors(a_plain[rows], p_plain[rows], ref),
                                "compensated": oracle_errors(a_comp[rows], p_comp[rows], ref)}
+        if newton is not None:
+            out["newton_step"]["oracle_error"] = oracle_errors(newton[2][rows], newton[3][rows], ref)
     print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -693,8 +728,10 @@ def main(argv=None):
     ap.add_argument("--no-tile-tune", dest="tile_tune", action="store_false")
     # Small-case options for profiler captures (the default run uses none).
     ap.add_argument("--n", type=int, default=0, help="override N (profiling small cases)")
-    ap.add_argument("--tile", default="", help="plain tile: threads,ipt,jtile,stages")
-    ap.add_argument("--tile-comp", default="", help="compensated tile: threads,ipt,jtile,stages")
+    ap.add_argument("--tile", default="", help="plain tile: the nb_tile fields, comma-separated")
+    ap.add_argument("--tile-comp", default="", help="compensated tile: the nb_tile fields")
+    ap.add_argument("--no-newton-arm", dest="newton_arm", action="store_false",
+                    help="skip timing the Newton-step tile beside the headline")
     ap.add_argument("--plain-only", action="store_true")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--sweep", action="store_true",

@@ -55,8 +55,9 @@ typedef enum nb_status {
 
 /*
  * Arithmetic variants of the pair kernel. Both keep every pair interaction in
- * FP32 (x_i - x_j, s, rsqrt on the special-function unit plus one
- * Newton-Raphson step, products) and add results in FP32.
+ * FP32 (x_i - x_j, s, rsqrt on the special-function unit, optionally refined
+ * by one Newton-Raphson step -- see nb_tile.refine -- and products) and add
+ * results in FP32.
  *  NB_PLAIN        two-level blocked sum: a register partial per j-tile, then
  *                  a running sum across tiles. Target: max per-particle
  *                  relative error <= 1e-5 against FP64.
@@ -81,7 +82,16 @@ typedef struct nb_ctx nb_ctx;
  * registers (0), and `packed` a bit mask of the interaction's operation
  * groups that run as packed FP32x2 instructions (1 difference, 2 distance,
  * 4 Newton step, 8 potential term, 16 force weight, 32 force accumulation;
- * the others run as scalar FP32; every mask gives bit-identical results). */
+ * the others run as scalar FP32; every mask gives bit-identical results),
+ * and `refine` the Newton-Raphson steps applied to the special-function
+ * unit's reciprocal square root (0 or 1). With refine = 0 a pair costs 13
+ * FP32 operations instead of 16 (mask bit 4 then has no effect). On sm_103a
+ * the unrefined estimate is within 2^-22.9 relative of 1/sqrt(s) (measured
+ * over every FP32 value in [1, 4), i.e. every mantissa and both exponent
+ * parities; the PTX ISA gives the same bound for the whole range), and one
+ * Newton step evaluated in FP32 does not lower that bound (its own three
+ * roundings are of the same size), so both settings meet the same error
+ * targets. A tile passed with fewer fields (zero-filled) means refine = 0. */
 typedef struct nb_tile {
     int threads;
     int ipt;
@@ -92,6 +102,7 @@ typedef struct nb_tile {
     int release;
     int sums_in_smem;
     int packed;
+    int refine;
 } nb_tile;
 
 /* Create a context on CUDA device `device`. *out receives the handle. */
@@ -190,6 +201,38 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
 nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
                            int64_t n, float eps, double dt, int nsteps, int a_valid,
                            nb_mode mode, void *stream);
+
+/*
+ * Reverse-mode gradient through nsteps leap-frog steps of nb_leapfrog_step
+ * (Eqs. (1)-(3) of Section "Method" with Eq. (gravity)), for one segment of a
+ * checkpointed trajectory. The segment is replayed from its entry state with
+ * the same kernels nb_leapfrog_step uses (so with the same positions), the
+ * positions of every step are kept, and the steps are then swept in reverse:
+ * per step, the adjoints of the two kicks and the drift (FP64 kernels) and
+ * one nb_force_vjp of the force at the step's end.
+ *   x, v  [n][3] FP64 device, in: the state at the segment's start
+ *   a     [n][3] FP32 device, in: Eq. (gravity) at x as the forward pass had
+ *                it (the a passed to nb_leapfrog_step with a_valid != 0), or
+ *                NULL if the forward computed it (a_valid == 0)
+ *   m     [n]    FP32 device masses
+ *   lx, lv [n][3] FP64 device, in/out: on entry dL/dx, dL/dv at the segment's
+ *                end; on exit at its start
+ *   la    [n][3] FP64 device, in/out: on entry dL/da for the force at the
+ *                segment's end (zero at the trajectory's end); on exit the
+ *                same for the force at its start
+ *   lm    [n]    FP64 device, in/out: dL/dm is added to it
+ *   apply_first  nonzero for the trajectory's first segment: the force at x
+ *                is itself a function of x and m, so its adjoint la is
+ *                folded into lx and lm by one more VJP and la is cleared
+ * mode, eps, dt, nsteps as passed to nb_leapfrog_step for the segment. The
+ * caller keeps (x, v, a) of each segment start from the forward pass.
+ * Scratch grows with (nsteps + 1) n 24 bytes (the positions kept).
+ * Asynchronous on `stream`; the caller's x, v, a are not modified.
+ */
+nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, const float *a,
+                              const float *m, int64_t n, float eps, double dt, int nsteps,
+                              double *lx, double *lv, double *la, double *lm, int apply_first,
+                              nb_mode mode, void *stream);
 
 /*
  * Total energy of an FP64 state: out_kw[0] = K = 1/2 sum m |v|^2 and

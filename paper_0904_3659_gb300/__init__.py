@@ -24,7 +24,8 @@ __all__ = [
     "NB_ERR_NOT_IMPLEMENTED", "NB_PLAIN", "NB_COMPENSATED", "NBError", "nb_tile",
     "library", "library_path", "exported_symbols", "Context",
     "nb_create", "nb_destroy", "nb_last_error", "nb_status_string", "nb_force",
-    "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_batched_step", "nb_leapfrog_step", "nb_energy",
+    "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_batched_step", "nb_leapfrog_step",
+    "nb_leapfrog_adjoint", "nb_energy",
     "nb_force_vjp", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_set_tuned_tile", "nb_list_tiles",
     "tune_to_file", "load_tuning",
     "nb_autotune", "nb_timing_enable", "nb_timing_read", "nb_timing_reset",
@@ -54,7 +55,7 @@ class nb_tile(ctypes.Structure):
                 ("jtile", ctypes.c_int), ("stages", ctypes.c_int),
                 ("unroll", ctypes.c_int), ("minblocks", ctypes.c_int),
                 ("release", ctypes.c_int), ("sums_in_smem", ctypes.c_int),
-                ("packed", ctypes.c_int)]
+                ("packed", ctypes.c_int), ("refine", ctypes.c_int)]
 
     def as_tuple(self):
         return tuple(getattr(self, f) for f, _ in self._fields_)
@@ -89,6 +90,8 @@ _SIGNATURES = {
                                     _c.c_int, _c.c_int, _c.c_int, _P]),
     "nb_leapfrog_batched_step": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _I64, _P, _P, _P,
                                             _c.c_double, _c.c_int, _c.c_int, _c.c_int, _P]),
+    "nb_leapfrog_adjoint": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _c.c_float, _c.c_double, _c.c_int,
+                                       _P, _P, _P, _P, _c.c_int, _c.c_int, _P]),
     "nb_energy": (_c.c_int, [_P, _P, _P, _P, _I64, _c.c_float, _P, _c.c_int, _P]),
     "nb_force_vjp": (_c.c_int, [_P, _P, _P, _I64, _c.c_float, _P, _P, _P, _P, _P]),
     "nb_synchronize": (_c.c_int, [_P, _P]),
@@ -225,6 +228,14 @@ def nb_leapfrog_step(ctx, x, v, m, a, p, n, eps, dt, nsteps, a_valid, mode=NB_PL
     _check(ctx, library().nb_leapfrog_step(ctx.handle, _addr(x), _addr(v), _addr(m), _addr(a),
                                            _addr(p), int(n), float(eps), float(dt), int(nsteps),
                                            int(a_valid), int(mode), _stream(stream)))
+
+
+def nb_leapfrog_adjoint(ctx, x, v, a, m, n, eps, dt, nsteps, lx, lv, la, lm, apply_first,
+                        mode=NB_PLAIN, stream=None):
+    _check(ctx, library().nb_leapfrog_adjoint(
+        ctx.handle, _addr(x), _addr(v), _addr(a), _addr(m), int(n), float(eps), float(dt),
+        int(nsteps), _addr(lx), _addr(lv), _addr(la), _addr(lm), int(bool(apply_first)), int(mode),
+        _stream(stream)))
 
 
 def nb_leapfrog_batched_step(ctx, x, v, m, offsets, n_clusters, n_total, eps, a, p, dt, nsteps,

@@ -2,19 +2,23 @@
 
 NBForce is a torch.autograd.Function whose forward is nb_force and whose
 backward is nb_force_vjp (the hand-written adjoint pair kernel), so gradients
-of any loss of a_i, p_i reach the positions and masses. leapfrog() chains
-kick-drift-kick steps (Section "Method", Eqs. (1)-(3) of Fujiwara & Nakasato,
-arXiv:0904.3659) on FP64 state with the FP32 force, recomputing each segment
-of `checkpoint_every` steps in the backward pass instead of storing it
-(torch.utils.checkpoint), so memory grows with the number of segments, not
-steps.
+of any loss of a_i, p_i reach the positions and masses.
+
+leapfrog() integrates kick-drift-kick steps (Section "Method", Eqs. (1)-(3)
+of Fujiwara & Nakasato, arXiv:0904.3659) on FP64 state with the FP32 force
+through nb_leapfrog_step, one call per segment of `checkpoint_every` steps,
+keeping only each segment's starting state. Its backward calls
+nb_leapfrog_adjoint per segment, last segment first: the library replays
+the segment and sweeps it in reverse with its own kernels, so memory grows
+with the number of segments (plus one segment's positions), not with the
+number of steps, and no step of the integrator runs as PyTorch arithmetic.
 """
 from __future__ import annotations
 
 import torch
-from torch.utils.checkpoint import checkpoint
 
-from . import NB_PLAIN, _default_context, nb_force, nb_force_vjp
+from . import (NB_PLAIN, _default_context, nb_force, nb_force_vjp, nb_leapfrog_adjoint,
+               nb_leapfrog_step)
 
 
 class NBForce(torch.autograd.Function):
@@ -52,26 +56,52 @@ def force(x, m, eps, mode=NB_PLAIN, nbctx=None):
     return NBForce.apply(x, m, eps, mode, nbctx)
 
 
-def _segment(x, v, a, m, eps, dt, nsteps, mode, nbctx):
-    for _ in range(nsteps):
-        v = v + (0.5 * dt) * (-a.double())        # Eq. (1)
-        x = x + dt * v                            # Eq. (2)
-        a, _ = NBForce.apply(x.float(), m, eps, mode, nbctx)
-        v = v + (0.5 * dt) * (-a.double())        # Eq. (3)
-    return x, v, a
+class Trajectory(torch.autograd.Function):
+    """(x, v) after nsteps leap-frog steps from FP64 (x0, v0) with FP32
+    masses m, differentiable in x0, v0 and m."""
+
+    @staticmethod
+    def forward(ctx, x0, v0, m, eps, dt, nsteps, checkpoint_every, mode, nbctx):
+        if nbctx is None:
+            nbctx = _default_context(x0.device.index or 0)
+        n = x0.shape[0]
+        m = m.detach().contiguous()
+        x = x0.detach().contiguous().clone()
+        v = v0.detach().contiguous().clone()
+        a = torch.empty((n, 3), dtype=torch.float32, device=x0.device)
+        seg = int(checkpoint_every) if checkpoint_every else max(int(nsteps), 1)
+        starts = []  # (x, v, a or None, steps) at each segment start
+        done = 0
+        while done < nsteps:
+            k = min(seg, nsteps - done)
+            first = not starts
+            starts.append((x.clone(), v.clone(), None if first else a.clone(), k))
+            nb_leapfrog_step(nbctx, x, v, m, a, None, n, eps, dt, k, 0 if first else 1, mode)
+            done += k
+        ctx.starts, ctx.m, ctx.nbctx = starts, m, nbctx
+        ctx.args = (float(eps), float(dt), int(mode))
+        return x, v
+
+    @staticmethod
+    def backward(ctx, gx, gv):
+        eps, dt, mode = ctx.args
+        m, n = ctx.m, ctx.m.shape[0]
+        dev = m.device
+        lx = (torch.zeros((n, 3), dtype=torch.float64, device=dev) if gx is None
+              else gx.to(torch.float64).contiguous().clone())
+        lv = (torch.zeros((n, 3), dtype=torch.float64, device=dev) if gv is None
+              else gv.to(torch.float64).contiguous().clone())
+        la = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        lm = torch.zeros((n,), dtype=torch.float64, device=dev)
+        for idx in reversed(range(len(ctx.starts))):
+            xs, vs, as_, k = ctx.starts[idx]
+            nb_leapfrog_adjoint(ctx.nbctx, xs, vs, as_, m, n, eps, dt, k, lx, lv, la, lm,
+                                apply_first=(idx == 0), mode=mode)
+        return lx, lv, lm.to(m.dtype), None, None, None, None, None, None
 
 
 def leapfrog(x0, v0, m, eps, dt, nsteps, checkpoint_every=8, mode=NB_PLAIN, nbctx=None):
     """nsteps KDK steps from FP64 (x0, v0) with FP32 masses m; differentiable
-    in x0, v0 and m. Returns (x, v) at the final time."""
-    a, _ = NBForce.apply(x0.float(), m, eps, mode, nbctx)
-    x, v = x0, v0
-    done = 0
-    while done < nsteps:
-        k = min(checkpoint_every, nsteps - done) if checkpoint_every else nsteps - done
-        if checkpoint_every and torch.is_grad_enabled():
-            x, v, a = checkpoint(_segment, x, v, a, m, eps, dt, k, mode, nbctx, use_reentrant=False)
-        else:
-            x, v, a = _segment(x, v, a, m, eps, dt, k, mode, nbctx)
-        done += k
-    return x, v
+    in x0, v0 and m. Returns (x, v) at the final time. checkpoint_every = 0
+    keeps no intermediate state (the backward replays all steps at once)."""
+    return Trajectory.apply(x0, v0, m, eps, dt, nsteps, checkpoint_every, mode, nbctx)

@@ -367,9 +367,11 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                 self0[q] = ibase + (2 * q) * 32 + lane - jbase;
                 self1[q] = self0[q] + 32;
             }
-            tile_pass<P, JT, 1, true, kMixAll>(T, xi, yi, zi, acc, eps2, self0, self1);
+            tile_pass<P, JT, 1, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
+                                                                    self1);
         } else {
-            tile_pass<P, JT, 4, false, kMixAll>(T, xi, yi, zi, acc, eps2, self0, self1);
+            tile_pass<P, JT, 4, false, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
+                                                                     self1);
         }
 #pragma unroll
         for (int q = 0; q < P; ++q)
@@ -400,7 +402,8 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
 }
 
 // Per particle: add the chunk sums of its (cluster, i-block) in chunk order
-// and remove the factor 4 of the acceleration. One block per cluster.
+// and remove the factors the pair sums carry (accel_scale, pot_scale of the
+// batched kernel's refine setting). One block per cluster.
 template <bool COMP>
 __global__ void batch_combine_kernel(const float4 *__restrict__ partial,
                                      const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
@@ -445,10 +448,11 @@ __global__ void batch_combine_kernel(const float4 *__restrict__ partial,
         }
         const int64_t gi = o + li;
         if (!NB_IN(err, 14, gi >= 0 && gi < n_total)) continue;
-        a[3 * gi + 0] = 0.25f * __fadd_rn(S[0], E[0]);
-        a[3 * gi + 1] = 0.25f * __fadd_rn(S[1], E[1]);
-        a[3 * gi + 2] = 0.25f * __fadd_rn(S[2], E[2]);
-        p[gi] = __fadd_rn(S[3], E[3]);
+        constexpr float as = accel_scale(kDefaultRefine), ps = pot_scale(kDefaultRefine);
+        a[3 * gi + 0] = as * __fadd_rn(S[0], E[0]);
+        a[3 * gi + 1] = as * __fadd_rn(S[1], E[1]);
+        a[3 * gi + 2] = as * __fadd_rn(S[2], E[2]);
+        p[gi] = ps * __fadd_rn(S[3], E[3]);
     }
 }
 

@@ -220,6 +220,8 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     ra.grid = plan.grid;
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
+    ra.a_scale = accel_scale(v.tile.refine);
+    ra.p_scale = pot_scale(v.tile.refine);
     ra.partial_len = pa.partial_len;
     ra.err = ctx->d_err;
     {
@@ -275,6 +277,8 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
     ra.perm = perm;
+    ra.a_scale = accel_scale(v.tile.refine);
+    ra.p_scale = pot_scale(v.tile.refine);
     ra.partial_len = pa.partial_len;
     ra.err = ctx->d_err;
     {

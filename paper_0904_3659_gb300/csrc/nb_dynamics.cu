@@ -91,6 +91,63 @@ __global__ void kick_kernel(double *__restrict__ v, const float *__restrict__ a,
     v[k] = v[k] + (0.5 * dt) * (-(double)a[k]);  // Eq. (3)
 }
 
+// Reverse sweep of one step (the adjoint of the kick-drift-kick step above,
+// with a_{t+1} = F(x_{t+1}) from Eq. (gravity) shared by the back kick of
+// step t and the front kick of step t+1). lx, lv, la are the adjoints of
+// x_{t+1}, v_{t+1} and a_{t+1} (la holding what the front kick of step t+1
+// contributed); all in FP64.
+// Before the force adjoint: the back kick v_{t+1} = v_h - dt/2 a_{t+1} adds
+// -dt/2 lv to la, and the operands of the VJP kernel are formed in FP32.
+__global__ void adj_back_kick_kernel(double *__restrict__ la, const double *__restrict__ lv,
+                                     const double *__restrict__ x_next, int64_t n, double dt,
+                                     float *__restrict__ ga32, float *__restrict__ x32) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const double l = la[k] + (-((0.5 * dt) * lv[k]));
+    la[k] = l;
+    ga32[k] = (float)l;
+    x32[k] = (float)x_next[k];
+}
+
+// After the force adjoint (gx, gm = VJP of Eq. (gravity) at x_{t+1} with
+// upstream la): lx += gx; the drift x_{t+1} = x_t + dt v_h adds dt lx to the
+// adjoint of v_h; the front kick v_h = v_t - dt/2 a_t passes it on to v_t
+// and gives a_t the adjoint -dt/2 lv. lm accumulates the mass gradient.
+__global__ void adj_drift_kick_kernel(double *__restrict__ lx, double *__restrict__ lv,
+                                      double *__restrict__ la, double *__restrict__ lm,
+                                      const float *__restrict__ gx, const float *__restrict__ gm,
+                                      int64_t n, double dt) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const double x = lx[k] + (double)gx[k];
+    const double v = lv[k] + dt * x;
+    lx[k] = x;
+    lv[k] = v;
+    la[k] = -((0.5 * dt) * v);
+    if (k < n) lm[k] = lm[k] + (double)gm[k];
+}
+
+// The force at the start of a trajectory, a_0 = F(x_0): VJP operands from
+// the adjoint of a_0, then its result folded into lx, lm (la cleared).
+__global__ void adj_first_operands_kernel(const double *__restrict__ la,
+                                          const double *__restrict__ x0, int64_t n,
+                                          float *__restrict__ ga32, float *__restrict__ x32) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    ga32[k] = (float)la[k];
+    x32[k] = (float)x0[k];
+}
+
+__global__ void adj_first_fold_kernel(double *__restrict__ lx, double *__restrict__ la,
+                                      double *__restrict__ lm, const float *__restrict__ gx,
+                                      const float *__restrict__ gm, int64_t n) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    lx[k] = lx[k] + (double)gx[k];
+    la[k] = 0.0;
+    if (k < n) lm[k] = lm[k] + (double)gm[k];
+}
+
 // Energy: per-block sums of K = 1/2 m |v|^2 and W = -1/2 m p in a fixed
 // tree order, then one block adds the block sums in order.
 constexpr int kEnergyThreads = 256;
@@ -145,7 +202,8 @@ enum Slot : int {
     S_P = SLOT_P,
     S_EBLK = SLOT_ENERGY_BLK,
     S_EOUT = SLOT_ENERGY_OUT,
-    S_PERM = SLOT_FRAMES
+    S_PERM = SLOT_FRAMES,
+    S_ADJ = SLOT_ADJOINT
 };
 
 void *slot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
@@ -211,17 +269,29 @@ nb_status steady_step(nb_ctx *ctx, double *x, double *v, const float *m, float *
     return run_force(ctx, nullptr, nullptr, jp, n, eps, a, p, comp, st);
 }
 
+// With x_hist set, copy the positions after step t (t = 0 for the entry
+// positions) into x_hist[t] ([nsteps + 1][n][3] FP64): the adjoint's replay.
+nb_status record(nb_ctx *ctx, double *x_hist, int t, const double *x, int64_t n, cudaStream_t s) {
+    if (!x_hist) return NB_OK;
+    const cudaError_t e = cudaMemcpyAsync(x_hist + (size_t)t * 3 * n, x, (size_t)3 * n * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? NB_OK : cuda_fail(ctx, e, "position history copy");
+}
+
 // The compensated leap-frog: the order is fixed for the call (from the entry
 // positions); every force evaluation re-packs offsets from the tiles'
-// reference points. Steps after the first are replayed from a graph.
+// reference points. Steps after the first are replayed from a graph, unless
+// the positions of every step are recorded (x_hist).
 nb_status leapfrog_frames(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
-                          int64_t n, float eps, double dt, int nsteps, int a_valid, cudaStream_t s) {
+                          int64_t n, float eps, double dt, int nsteps, int a_valid, cudaStream_t s,
+                          double *x_hist) {
     Frames f;
     nb_status st = reserve_frames_state(ctx, n, &f);
     if (st != NB_OK) return st;
     cudaError_t e = launch_spatial_order(x, n, f.order_scratch, f.perm, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ordering launch");
     if (!a_valid && (st = force_frames(ctx, x, m, f, n, eps, a, p, s)) != NB_OK) return st;
+    if ((st = record(ctx, x_hist, 0, x, n, s)) != NB_OK) return st;
     if (nsteps == 0) return NB_OK;
     const unsigned nb3 = blocks_for(3 * n, 256);
     auto step = [&](int kick_back) -> nb_status {
@@ -230,9 +300,9 @@ nb_status leapfrog_frames(nb_ctx *ctx, double *x, double *v, const float *m, flo
         if (le != cudaSuccess) return cuda_fail(ctx, le, "leap-frog update launch");
         return force_frames(ctx, x, m, f, n, eps, a, p, s);
     };
-    if ((st = step(0)) != NB_OK) return st;
+    if ((st = step(0)) != NB_OK || (st = record(ctx, x_hist, 1, x, n, s)) != NB_OK) return st;
     const int rest = nsteps - 1;
-    if (rest >= 2 && s != nullptr) {
+    if (rest >= 2 && s != nullptr && !x_hist) {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -254,10 +324,85 @@ nb_status leapfrog_frames(nb_ctx *ctx, double *x, double *v, const float *m, flo
         if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
     } else {
         for (int k = 0; k < rest; ++k)
-            if ((st = step(1)) != NB_OK) return st;
+            if ((st = step(1)) != NB_OK || (st = record(ctx, x_hist, k + 2, x, n, s)) != NB_OK)
+                return st;
     }
     kick_kernel<<<nb3, 256, 0, s>>>(v, a, n, dt);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "kick launch");
+    return NB_OK;
+}
+
+// The plain leap-frog (scratch reserved by the caller): fused kicks, drift
+// and FP32 packing, then the pair kernel. Steps after the first are replayed
+// from a graph unless the positions of every step are recorded (x_hist).
+nb_status leapfrog_plain(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
+                         int64_t n, float eps, double dt, int nsteps, int a_valid, cudaStream_t s,
+                         double *x_hist) {
+    JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
+    cudaError_t e;
+    nb_status st;
+    if (!a_valid) {
+        pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "pack launch");
+        if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, a, p, false, s)) != NB_OK) return st;
+    }
+    if ((st = record(ctx, x_hist, 0, x, n, s)) != NB_OK) return st;
+    if (nsteps == 0) return NB_OK;
+
+    // Step 0: front kick + drift + pack, force.
+    kick_drift_pack_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, v, a, m, n, padded(n), dt, 0,
+                                                                      jp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "leap-frog update launch");
+    if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, a, p, false, s)) != NB_OK) return st;
+    if ((st = record(ctx, x_hist, 1, x, n, s)) != NB_OK) return st;
+
+    // Steps 1 .. nsteps-1: the same kernels with the same arguments each
+    // step, so they are captured once into a graph and replayed (not on the
+    // legacy default stream, which cannot be captured).
+    const int rest = nsteps - 1;
+    if (rest >= 2 && s != nullptr && !x_hist) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
+        const bool timing = ctx_set_timing(ctx, false);  // no event nodes in the graph
+        nb_status cst = steady_step(ctx, x, v, m, a, p, n, eps, dt, false, s);
+        ctx_set_timing(ctx, timing);
+        e = cudaStreamEndCapture(s, &graph);
+        if (cst != NB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cst;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+        for (int k = 0; k < rest && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    } else {
+        for (int k = 0; k < rest; ++k)
+            if ((st = steady_step(ctx, x, v, m, a, p, n, eps, dt, false, s)) != NB_OK ||
+                (st = record(ctx, x_hist, k + 2, x, n, s)) != NB_OK)
+                return st;
+    }
+    // Final back kick, Eq. (3).
+    kick_kernel<<<blocks_for(3 * n, 256), 256, 0, s>>>(v, a, n, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "kick launch");
+    return NB_OK;
+}
+
+// Scratch of a leap-frog call (before any graph capture); *pbuf receives the
+// potential array to use (the caller's, else the context's).
+nb_status reserve_leapfrog(nb_ctx *ctx, int64_t n, nb_mode mode, float *p, float **pbuf) {
+    nb_status st;
+    if ((st = reserve_force(ctx, n, mode == NB_COMPENSATED)) != NB_OK) return st;
+    if ((st = nb_reserve(ctx, n, mode)) != NB_OK) return st;
+    *pbuf = p;
+    if (!p) {
+        if ((st = ensure_slot(ctx, S_P, (size_t)n * sizeof(float))) != NB_OK) return st;
+        *pbuf = static_cast<float *>(slot(ctx, S_P));
+    }
     return NB_OK;
 }
 
@@ -277,65 +422,78 @@ nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, fl
     if (!x || !v || !m || !a) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const bool comp = mode == NB_COMPENSATED;
-
     // Scratch first (allocation never happens inside the captured graph).
-    if ((st = reserve_force(ctx, n, comp)) != NB_OK) return st;
-    if ((st = nb_reserve(ctx, n, mode)) != NB_OK) return st;
-    float *pbuf = p;
-    if (!pbuf) {
-        if ((st = ensure_slot(ctx, S_P, (size_t)n * sizeof(float))) != NB_OK) return st;
-        pbuf = static_cast<float *>(slot(ctx, S_P));
+    float *pbuf = nullptr;
+    if ((st = reserve_leapfrog(ctx, n, mode, p, &pbuf)) != NB_OK) return st;
+    if (mode == NB_COMPENSATED)
+        return leapfrog_frames(ctx, x, v, m, a, pbuf, n, eps, dt, nsteps, a_valid, s, nullptr);
+    return leapfrog_plain(ctx, x, v, m, a, pbuf, n, eps, dt, nsteps, a_valid, s, nullptr);
+}
+
+nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, const float *a,
+                              const float *m, int64_t n, float eps, double dt, int nsteps,
+                              double *lx, double *lv, double *la, double *lm, int apply_first,
+                              nb_mode mode, void *stream) {
+    if (!ctx) return NB_ERR_ARG;
+    nb_status st = check_common(ctx, n, eps, mode);
+    if (st != NB_OK) return st;
+    if (nsteps < 0) return fail(ctx, NB_ERR_ARG, "nsteps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ctx, NB_ERR_ARG, "dt must be finite");
+    if (n == 0) return NB_OK;
+    if (!x || !v || !m || !lx || !lv || !la || !lm) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    DeviceGuard g(ctx_device(ctx));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n3 = (size_t)3 * n;
+
+    // One scratch buffer: replayed x, v (FP64), positions of every step
+    // (FP64), replayed a, p and the VJP kernel's operands and results (FP32).
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_xv = al(n3 * sizeof(double)), b_hist = al((size_t)(nsteps + 1) * n3 * sizeof(double));
+    const size_t b_v3 = al(n3 * sizeof(float)), b_s = al((size_t)n * sizeof(float));
+    const size_t total = 2 * b_xv + b_hist + 4 * b_v3 + 3 * b_s;
+    if ((st = ensure_slot(ctx, S_ADJ, total)) != NB_OK) return st;
+    float *pbuf = nullptr;
+    if ((st = reserve_leapfrog(ctx, n, mode, nullptr, &pbuf)) != NB_OK) return st;
+    unsigned char *base = static_cast<unsigned char *>(slot(ctx, S_ADJ));
+    double *xw = reinterpret_cast<double *>(base);
+    double *vw = reinterpret_cast<double *>(base + b_xv);
+    double *hist = reinterpret_cast<double *>(base + 2 * b_xv);
+    float *aw = reinterpret_cast<float *>(base + 2 * b_xv + b_hist);
+    float *x32 = aw + b_v3 / sizeof(float);
+    float *ga32 = x32 + b_v3 / sizeof(float);
+    float *gx32 = ga32 + b_v3 / sizeof(float);
+    float *gp32 = gx32 + b_v3 / sizeof(float);
+    float *gm32 = gp32 + b_s / sizeof(float);
+    float *pw = gm32 + b_s / sizeof(float);
+
+    // Replay the segment on copies with the forward's own kernels (same
+    // order and reference frames, so the same positions), recording x.
+    cudaError_t e = cudaMemcpyAsync(xw, x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vw, v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && a) e = cudaMemcpyAsync(aw, a, n3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gp32, 0, (size_t)n * sizeof(float), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint replay copies");
+    st = mode == NB_COMPENSATED
+             ? leapfrog_frames(ctx, xw, vw, m, aw, pw, n, eps, dt, nsteps, a != nullptr, s, hist)
+             : leapfrog_plain(ctx, xw, vw, m, aw, pw, n, eps, dt, nsteps, a != nullptr, s, hist);
+    if (st != NB_OK) return st;
+
+    // Reverse sweep, last step first: one VJP of Eq. (gravity) per step.
+    const unsigned nb3 = blocks_for((int64_t)n3, 256);
+    for (int t = nsteps - 1; t >= 0; --t) {
+        adj_back_kick_kernel<<<nb3, 256, 0, s>>>(la, lv, hist + (size_t)(t + 1) * n3, n, dt, ga32, x32);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint kick launch");
+        if ((st = nb_force_vjp(ctx, x32, m, n, eps, ga32, gp32, gx32, gm32, stream)) != NB_OK) return st;
+        adj_drift_kick_kernel<<<nb3, 256, 0, s>>>(lx, lv, la, lm, gx32, gm32, n, dt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint drift launch");
     }
-    JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
-    cudaError_t e;
-
-    if (comp) return leapfrog_frames(ctx, x, v, m, a, pbuf, n, eps, dt, nsteps, a_valid, s);
-
-    if (!a_valid) {
-        pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "pack launch");
-        if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, a, pbuf, comp, s)) != NB_OK) return st;
+    if (apply_first) {
+        adj_first_operands_kernel<<<nb3, 256, 0, s>>>(la, hist, n, ga32, x32);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
+        if ((st = nb_force_vjp(ctx, x32, m, n, eps, ga32, gp32, gx32, gm32, stream)) != NB_OK) return st;
+        adj_first_fold_kernel<<<nb3, 256, 0, s>>>(lx, la, lm, gx32, gm32, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }
-    if (nsteps == 0) return NB_OK;
-
-    // Step 0: front kick + drift + pack, force.
-    kick_drift_pack_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, v, a, m, n, padded(n), dt, 0,
-                                                                      jp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "leap-frog update launch");
-    if ((st = run_force(ctx, nullptr, nullptr, jp, n, eps, a, pbuf, comp, s)) != NB_OK) return st;
-
-    // Steps 1 .. nsteps-1: the same kernels with the same arguments each
-    // step, so they are captured once into a graph and replayed (not on the
-    // legacy default stream, which cannot be captured).
-    const int rest = nsteps - 1;
-    if (rest >= 2 && s != nullptr) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture begin");
-        const bool timing = ctx_set_timing(ctx, false);  // no event nodes in the graph
-        nb_status cst = steady_step(ctx, x, v, m, a, pbuf, n, eps, dt, comp, s);
-        ctx_set_timing(ctx, timing);
-        e = cudaStreamEndCapture(s, &graph);
-        if (cst != NB_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return cst;
-        }
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture end");
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
-        for (int k = 0; k < rest && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
-        cudaGraphExecDestroy(exec);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
-    } else {
-        for (int k = 0; k < rest; ++k)
-            if ((st = steady_step(ctx, x, v, m, a, pbuf, n, eps, dt, comp, s)) != NB_OK) return st;
-    }
-    // Final back kick, Eq. (3).
-    kick_kernel<<<blocks_for(3 * n, 256), 256, 0, s>>>(v, a, n, dt);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "kick launch");
     return NB_OK;
 }
 

@@ -26,6 +26,7 @@ enum ExtSlot : int {
     SLOT_VJP_VP,        // packed VJP records
     SLOT_VJP_PART,      // VJP partial sums
     SLOT_FRAMES,        // permutation, ordering scratch, reference points
+    SLOT_ADJOINT,       // leap-frog adjoint: replayed state, position history, VJP operands
     SLOT_COUNT
 };
 

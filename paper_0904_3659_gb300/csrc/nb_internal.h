@@ -12,8 +12,9 @@ namespace nbk {
 // One particle as staged in shared memory for the pair kernel: 32 bytes,
 // every value duplicated so that one 64-bit register pair feeds both lanes
 // of a packed FP32x2 instruction. Positions are stored negated and the mass
-// as -m/2 (both exact): d = x_i + (-x_j) and the Newton step folds the
-// factor -1/2 into the mass (see nb_pair.cu).
+// as -m/2 (both exact): d = x_i + (-x_j); the Newton step folds its factor
+// -1/2 into the mass, and without the step the sums carry -1/2, which the
+// combine removes (see tile_pass).
 struct alignas(32) JPart {
     float2 nx, ny, nz, hm;
 };
@@ -56,6 +57,8 @@ struct ReduceArgs {
     int maxseg;
     int ib;
     const int32_t *perm;   // if set, result k is written to particle perm[k]
+    float a_scale;         // sums -> a_i and p_i: accel_scale / pot_scale of
+    float p_scale;         //   the pair variant's refine setting
     int64_t partial_len;   // float4 entries of partial (debug build)
     int *err;              // device error word (debug build)
 };
@@ -63,8 +66,19 @@ struct ReduceArgs {
 inline bool same_tile(const nb_tile &a, const nb_tile &b) {
     return a.threads == b.threads && a.ipt == b.ipt && a.jtile == b.jtile && a.stages == b.stages &&
            a.unroll == b.unroll && a.minblocks == b.minblocks && a.release == b.release &&
-           a.sums_in_smem == b.sums_in_smem && a.packed == b.packed;
+           a.sums_in_smem == b.sums_in_smem && a.packed == b.packed && a.refine == b.refine;
 }
+
+// Factors that turn the pair kernels' sums into a_i and p_i (exact powers of
+// two). With the Newton step the sums hold 4 a_i and p_i; without it they
+// hold -a_i/2 and -p_i/2, because the packed mass is -m/2 (see tile_pass).
+__host__ __device__ constexpr float accel_scale(int refine) { return refine ? 0.25f : -2.0f; }
+__host__ __device__ constexpr float pot_scale(int refine) { return refine ? 1.0f : -2.0f; }
+
+// Newton steps of the built-in default shapes and of the fixed-shape kernels
+// (batched, frames, allocation-free): none, since on sm_103a the step does
+// not improve the FP32 result (see nb_tile.refine).
+constexpr int kDefaultRefine = 0;
 
 // A compiled pair-kernel shape.
 struct PairVariant {

@@ -144,6 +144,8 @@ extern "C" nb_status nb_force_noalloc(const float *x, const float *m, int64_t n,
     ra.grid = plan.grid;
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
+    ra.a_scale = accel_scale(v.tile.refine);
+    ra.p_scale = pot_scale(v.tile.refine);
     ra.partial_len = pa.partial_len;
     ra.err = ds.err;
     e = launch_reduce(ra, false, st);

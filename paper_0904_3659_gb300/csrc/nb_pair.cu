@@ -18,16 +18,21 @@
 //    N divides. A CTA that covers only part of an i-block's j range writes a
 //    partial sum; a second kernel adds the partials of each i-block in CTA
 //    order. No float atomics: results are bit-reproducible for a fixed launch.
-//  * Per interaction: 16 FP32 lane operations + 1 reciprocal square root:
+//  * Per interaction: 13 FP32 lane operations + 1 reciprocal square root,
+//    or 16 with the optional Newton step (template knob NEWTON):
 //      d  = x_i - x_j                      3 add
 //      s  = eps^2 + d.d                    3 fma
 //      y  = rsqrt(s)                       1 special-function op
-//      Newton step folded into the mass:   y2 = y*y, t = s*y2 - 3, u = y*t
-//        (the refined value is y1 = -u/2, see tile_pass)
-//      q  = (-m_j/2) * u = m_j y1          1 mul     p_i += q   1 add
-//      w  = q * u*u     = 4 m_j y1^3       2 mul
+//      NEWTON, folded into the mass:       y2 = y*y, t = s*y2 - 3, u = y*t
+//        (the refined value is y1 = -u/2, see tile_pass); else u = y
+//      q  = (-m_j/2) * u                   1 mul     p_i += q   1 add
+//      w  = q * u*u                        2 mul
 //      a_i += w d                           3 fma
-//    a_i carries a factor 4 that the combine removes (an exact scaling).
+//    The sums carry a factor (4 for a and 1 for p with NEWTON, -1/2 for both
+//    without) that the combine removes, an exact scaling. On sm_103a the
+//    special-function unit's estimate is already within 2^-22.9 of s^{-1/2}
+//    and the FP32 Newton step does not improve on it, so the built-in
+//    shapes omit it.
 #include <algorithm>
 #include <cstdio>
 
@@ -75,13 +80,14 @@ __global__ void pack_f32_kernel(const float *__restrict__ x, const float *__rest
 //                 tiles: 0 registers, 1 shared memory (one slot per thread,
 //                 touched once per tile; frees 8-16 registers per i-particle)
 //   MIX           which op groups of an interaction run packed (see kMix*)
+//   NEWTON        one Newton-Raphson step on the reciprocal square root
 //   COMP          Kahan-compensated running sums (NB_COMPENSATED)
 //   FR            positions are packed as FP32 offsets from per-j-tile
 //                 reference points args.cref; before each tile the thread
 //                 re-centres its i-particles on that tile's point:
 //                 x~_i = delta_i + (c_I - c_J), I the tile holding i.
 template <int THREADS, int IPT, int JT, int STAGES, int UNR, int MINB, int REL, int ACCS, int MIX,
-          bool COMP, bool FR>
+          bool NEWTON, bool COMP, bool FR>
 __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args) {
     static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
     constexpr int P = IPT / 2;
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
 
     float2 xi[P], yi[P], zi[P];
     float2 cix[P], ciy[P], ciz[P];  // FR: reference point of each i's own tile
-    float2 sum[P][4], cmp[P][4];
+    float2 sum[P][4] = {}, cmp[P][4] = {};  // unused when the sums live in shared memory
     const float2 eps2 = splat2(args.eps2);
     const float2 zero2 = splat2(0.f);
 
@@ -263,9 +269,9 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
                 self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
                 self1[q] = self0[q] + THREADS;
             }
-            tile_pass<P, JT, 1, true, MIX>(T, xr, yr, zr, acc, eps2, self0, self1);
+            tile_pass<P, JT, 1, true, MIX, NEWTON>(T, xr, yr, zr, acc, eps2, self0, self1);
         } else {
-            tile_pass<P, JT, UNR, false, MIX>(T, xr, yr, zr, acc, eps2, self0, self1);
+            tile_pass<P, JT, UNR, false, MIX, NEWTON>(T, xr, yr, zr, acc, eps2, self0, self1);
         }
 
         if (REL == 1) {
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
 
 // ---------------------------------------------------------------------------
 // Combine: for each i, add the partials of its i-block in CTA order and
-// remove the factor 4 carried by the acceleration sums.
+// remove the factors the pair kernel's sums carry (r.a_scale, r.p_scale).
 __device__ __forceinline__ int64_t cta_of_unit(int64_t u, int64_t units, int grid) {
     return ((u + 1) * (int64_t)grid - 1) / units;
 }
@@ -345,10 +351,10 @@ __global__ void reduce_plain_kernel(const ReduceArgs r) {
     }
     const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
     if (!NB_IN(r.err, 6, o >= 0 && o < r.n)) return;
-    r.a[3 * o + 0] = 0.25f * ax;
-    r.a[3 * o + 1] = 0.25f * ay;
-    r.a[3 * o + 2] = 0.25f * az;
-    r.p[o] = pp;
+    r.a[3 * o + 0] = r.a_scale * ax;
+    r.a[3 * o + 1] = r.a_scale * ay;
+    r.a[3 * o + 2] = r.a_scale * az;
+    r.p[o] = r.p_scale * pp;
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -385,10 +391,10 @@ __global__ void reduce_comp_kernel(const ReduceArgs r) {
     }
     const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
     if (!NB_IN(r.err, 6, o >= 0 && o < r.n)) return;
-    r.a[3 * o + 0] = 0.25f * __fadd_rn(S[0], E[0]);
-    r.a[3 * o + 1] = 0.25f * __fadd_rn(S[1], E[1]);
-    r.a[3 * o + 2] = 0.25f * __fadd_rn(S[2], E[2]);
-    r.p[o] = __fadd_rn(S[3], E[3]);
+    r.a[3 * o + 0] = r.a_scale * __fadd_rn(S[0], E[0]);
+    r.a[3 * o + 1] = r.a_scale * __fadd_rn(S[1], E[1]);
+    r.a[3 * o + 2] = r.a_scale * __fadd_rn(S[2], E[2]);
+    r.p[o] = r.p_scale * __fadd_rn(S[3], E[3]);
 }
 
 // Synthetic inputs for tuning runs (timing only; values do not matter
@@ -408,9 +414,9 @@ __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed
 
 // ---------------------------------------------------------------------------
 // Launchers and the registry of compiled shapes.
-template <int T, int I, int J, int S, int U, int M, int R, int A, int X, bool C, bool F>
+template <int T, int I, int J, int S, int U, int M, int R, int A, int X, bool N, bool C, bool F>
 static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
-    pair_kernel<T, I, J, S, U, M, R, A, X, C, F><<<grid, T, smem, st>>>(a);
+    pair_kernel<T, I, J, S, U, M, R, A, X, N, C, F><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -421,44 +427,73 @@ constexpr size_t pair_smem() {
            (size_t)S * sizeof(uint64_t) + (2 * S + 1) * sizeof(int);
 }
 
-#define NB_VARIANT_F(T, I, J, S, U, M, R, A, X, C, F)                                           \
-    {{T, I, J, S, U, M, R, A, X}, C, (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, C, F>,   \
-     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, C, F>}
-#define NB_VARIANT(T, I, J, S, U, M, R, A, X, C) NB_VARIANT_F(T, I, J, S, U, M, R, A, X, C, false)
+// One registry entry: tile fields in nb_tile order (refine last), then the
+// compensated and frames flags.
+#define NB_VARIANT_F(T, I, J, S, U, M, R, A, X, N, C, F)                                       \
+    {{T, I, J, S, U, M, R, A, X, N}, C,                                                         \
+     (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, (N != 0), C, F>,                      \
+     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, (N != 0), C, F>}
+#define NB_VARIANT(T, I, J, S, U, M, R, A, X, N, C) NB_VARIANT_F(T, I, J, S, U, M, R, A, X, N, C, false)
 
-// Plain shapes: entry 0 is the large-n default, entry 1 the small-n default.
-// (Measured on GB300 at N = 2^18 and 2^20: the all-packed mask 63 beats every
-// scalar or mixed mask; IPT 6-12 with ~2 warps per scheduler are fastest.)
+// Plain shapes. The first group evaluates the reciprocal square root without
+// the Newton step (refine 0, 13 FP32 ops per pair); the second keeps the
+// step (16 ops) for comparison and for callers that ask for it. Measured on
+// GB300 with the step: the all-packed mask 63 beats every scalar or mixed
+// mask; IPT 6-12 with ~2 warps per scheduler are fastest at large n.
 static const PairVariant kPlain[] = {
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 63, false),
-    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, false),
-    NB_VARIANT(128, 8, 512, 3, 8, 1, 0, 0, 63, false),
-    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, 63, false),
-    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, false),
-    NB_VARIANT(128, 6, 256, 3, 8, 1, 1, 1, 63, false),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 0, false),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 28, false),
-    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, false),
-    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, false),
-    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, false),
-    NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, 63, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 63, 0, false),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 1, 1, 63, 0, false),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, 0, false),
+    NB_VARIANT(128, 8, 512, 3, 8, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, 0, false),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(256, 4, 256, 3, 4, 2, 0, 0, 63, 0, false),
+    NB_VARIANT(128, 4, 256, 3, 4, 4, 0, 0, 63, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 3, 1, 0, 63, 0, false),
+    NB_VARIANT(128, 6, 256, 3, 4, 3, 0, 1, 63, 0, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 63, 1, false),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, 1, false),
+    NB_VARIANT(128, 8, 512, 3, 8, 1, 0, 0, 63, 1, false),
+    NB_VARIANT(128, 8, 256, 3, 4, 1, 0, 0, 63, 1, false),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, 1, false),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 1, 1, 63, 1, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 0, 1, false),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 0, 28, 1, false),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, 1, false),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, 1, false),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, 1, false),
+    NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, 63, 1, false),
 };
 static const PairVariant kComp[] = {
-    NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, true),
-    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, true),
-    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, true),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, true),
-    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, true),
-    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 0, true),
-    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, 63, true),
-    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, true),
-    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, true),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, 0, true),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, 0, true),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, 0, true),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, 0, true),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, 0, true),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, 0, true),
+    NB_VARIANT(256, 4, 256, 3, 4, 2, 0, 0, 63, 0, true),
+    NB_VARIANT(128, 4, 256, 3, 4, 4, 0, 0, 63, 0, true),
+    NB_VARIANT(128, 6, 256, 3, 4, 3, 0, 1, 63, 0, true),
+    NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 1, true),
+    NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, 1, true),
+    NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, 1, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, 1, true),
+    NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, 1, true),
+    NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 0, 1, true),
+    NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, 63, 1, true),
+    NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, 1, true),
+    NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, 1, true),
 };
 // Frame variants (compensated, per-tile reference points; jtile must be 256,
 // the only tile length the frames pack is compiled for).
 static const PairVariant kFrames[] = {
-    NB_VARIANT_F(128, 6, 256, 3, 8, 1, 0, 1, 63, true, true),  // large n
-    NB_VARIANT_F(64, 4, 256, 3, 4, 1, 0, 1, 63, true, true),   // small n
+    NB_VARIANT_F(256, 4, 256, 3, 4, 1, 0, 0, 63, kDefaultRefine, true, true),  // large n
+    NB_VARIANT_F(64, 4, 256, 3, 4, 1, 0, 1, 63, kDefaultRefine, true, true),   // small n
 };
 #undef NB_VARIANT
 #undef NB_VARIANT_F
@@ -474,21 +509,36 @@ const PairVariant *pair_variant(bool comp, int idx) {
     return comp ? &kComp[idx] : &kPlain[idx];
 }
 
-const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
-    for (int k = 0; k < pair_variant_count(comp); ++k) {
-        const nb_tile &v = pair_variant(comp, k)->tile;
-        if (same_tile(v, t)) return pair_variant(comp, k);
-    }
-    return nullptr;
+static int pair_variant_index(bool comp, const nb_tile &t) {
+    for (int k = 0; k < pair_variant_count(comp); ++k)
+        if (same_tile(pair_variant(comp, k)->tile, t)) return k;
+    return -1;
 }
 
-// Built-in choices per size class, from the measured shape sweep (GB300):
-// short tiles with 2 i per thread while the work cannot fill the GPU with
-// large i-blocks, the 6-8 i per thread shapes from N = 2^15 on.
+const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
+    return pair_variant(comp, pair_variant_index(comp, t));
+}
+
+// Built-in choices per size class, from the measured shape sweep (GB300,
+// no Newton step): 2 i per thread and 128-particle tiles while the work
+// cannot fill 152 SMs with large i-blocks, then 4 i per thread in 256-thread
+// CTAs; the plain sums from N = 2^17 on take 12 i per thread with the
+// running sums in shared memory.
 int pair_default_index(bool comp, int64_t n) {
-    if (n >= (int64_t)1 << 15) return 0;
-    if (comp) return n >= (int64_t)1 << 13 ? 1 : 8;   // (64,2,64,4) / (128,2,128,4)
-    return n >= (int64_t)1 << 13 ? 10 : 9;            // (128,2,128,4) / (256,2,128,4)
+    constexpr int R = kDefaultRefine;
+    static const nb_tile shapes[2][4] = {
+        {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {64, 4, 128, 4, 4, 1, 0, 0, 63, R},
+         {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {128, 12, 256, 3, 4, 1, 0, 1, 63, R}},
+        {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R},
+         {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R}}};
+    static const int idx[2][4] = {
+        {pair_variant_index(false, shapes[0][0]), pair_variant_index(false, shapes[0][1]),
+         pair_variant_index(false, shapes[0][2]), pair_variant_index(false, shapes[0][3])},
+        {pair_variant_index(true, shapes[1][0]), pair_variant_index(true, shapes[1][1]),
+         pair_variant_index(true, shapes[1][2]), pair_variant_index(true, shapes[1][3])}};
+    const int cls = n >= (int64_t)1 << 17 ? 3 : n >= (int64_t)1 << 15 ? 2 : n >= (int64_t)1 << 13 ? 1 : 0;
+    const int k = idx[comp ? 1 : 0][cls];
+    return k >= 0 ? k : 0;  // every default above is compiled; 0 guards a stale edit
 }
 
 PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {

@@ -9,12 +9,15 @@
 namespace nbk {
 using namespace nbdev;
 
-// One pass of a j-tile against the thread's P pairs of i-particles.
-// acc[q][0..2] += 4 m_j y1^3 (x_i - x_j), acc[q][3] += m_j y1, where
-// y1 = y (3 - s y^2) / 2 is one Newton-Raphson step for f(y) = y^-2 - s from
-// the special-function unit's estimate y of s^{-1/2}. With t = s y^2 - 3 and
-// u = y t we have y1 = -u/2, so m_j y1 = (-m_j/2) u (the packed mass is
-// stored as -m_j/2) and 4 m_j y1^3 = (m_j y1) u^2.
+// One pass of a j-tile against the thread's P pairs of i-particles, with y
+// the special-function unit's estimate of s^{-1/2}.
+// NEWTON: acc[q][0..2] += 4 m_j y1^3 (x_i - x_j), acc[q][3] += m_j y1, where
+// y1 = y (3 - s y^2) / 2 is one Newton-Raphson step for f(y) = y^-2 - s.
+// With t = s y^2 - 3 and u = y t we have y1 = -u/2, so m_j y1 = (-m_j/2) u
+// (the packed mass is stored as -m_j/2) and 4 m_j y1^3 = (m_j y1) u^2:
+// 16 FP32 operations per pair.
+// Without the step: q = (-m_j/2) y, acc[q][3] += q, acc[q][0..2] += q y^2
+// (x_i - x_j), i.e. the sums hold -p_i/2 and -a_i/2: 13 FP32 operations.
 // In a diagonal tile (DIAG) the j == i term is removed by zeroing the mass
 // lane of the thread's own particle; self0/self1 give, per pair, the tile
 // position of the thread's own i (outside [0, JT) when it is not here).
@@ -38,7 +41,7 @@ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
     return PK ? fma2(a, b, c) : make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
 }
 
-template <int P, int JT, int UNR, bool DIAG, int MIX>
+template <int P, int JT, int UNR, bool DIAG, int MIX, bool NEWTON>
 __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const float2 (&xi)[P],
                                           const float2 (&yi)[P], const float2 (&zi)[P],
                                           float2 (&acc)[P][4], const float2 eps2,
@@ -63,9 +66,12 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
             s = vfma<PS>(dy, dy, s);
             s = vfma<PS>(dz, dz, s);
             const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
-            const float2 y2 = vmul<PN>(y, y);
-            const float2 t = vfma<PN>(s, y2, m3);
-            const float2 u = vmul<PN>(y, t);
+            float2 u = y;
+            if (NEWTON) {
+                const float2 y2 = vmul<PN>(y, y);
+                const float2 t = vfma<PN>(s, y2, m3);
+                u = vmul<PN>(y, t);
+            }
             float2 hm = hmj;
             if (DIAG) {
                 if (jj == self0[q]) hm.x = 0.f;

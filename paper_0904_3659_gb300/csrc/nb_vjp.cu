@@ -11,15 +11,20 @@
 // Regrouped per pair into a coefficient of r and three sums:
 //   gx_i = ga_i sum_l m_l y^3 - m_i sum_l y^3 ga_l + sum_l c_il r
 //   c_il = 3 y^5 (m_i r.ga_l - m_l r.ga_i) - y^3 (gp_i m_l + m_i gp_l)
-// With the Newton-refined y1 = -u/2 (u as in the force kernel): y^3 = -u^3/8,
-// y^5 = -u^5/32, so
-//   32 c_il = u^5 (m_l (3 ga_i).r + (-3 m_i) ga_l.r) + u^3 (4 gp_i m_l + (-m_i)(-4 gp_l))
-// The kernel accumulates, per i,
-//   R = sum 32 c_il r,  S = sum m_l u^3,  V = sum u^3 ga_l,
-//   G = sum ((r.ga_l) u^3 + (-4 gp_l) u)
-// and the combine forms gx_i = R/32 - ga_i S/8 + m_i V/8, gm_i = G/8
-// (the 1/8 and 1/32 are exact scalings). 33 FP32 operations and one
-// special-function reciprocal square root per pair.
+// The kernel forms, per pair, with the packed gradient value h_l (below) and
+// u the reciprocal square root in the form chosen by kVNewton,
+//   C = u^5 (m_l (3 ga_i).r + (-3 m_i) ga_l.r) + u^3 (h_i' m_l + (-m_i) h_l)
+// and accumulates, per i,
+//   R = sum C r,  S = sum m_l u^3,  V = sum u^3 ga_l,  G = sum ((r.ga_l) u^3 + h_l u)
+// where h_i' = -h_i is read back from particle i's own record.
+//  * Without the Newton step (the default): u = y, h_l = -gp_l, so C = -c_il,
+//    G = -gm_i and gx_i = -R + ga_i S - m_i V, gm_i = -G; 30 FP32 operations
+//    per pair.
+//  * With it: u = -2 y1 (y1 the refined value, as in the force kernel),
+//    h_l = -4 gp_l: y^3 = -u^3/8 and y^5 = -u^5/32 give C = 32 c_il, G = 8 gm_i,
+//    so gx_i = R/32 - ga_i S/8 + m_i V/8, gm_i = G/8; 33 operations.
+// All scale factors are exact powers of two; one special-function
+// reciprocal square root per pair.
 #include <algorithm>
 #include <cmath>
 
@@ -30,8 +35,17 @@
 namespace nbk {
 using namespace nbdev;
 
+// Newton step on the reciprocal square root (see the header comment).
+constexpr bool kVNewton = kDefaultRefine != 0;
+// Packed gradient value h = kVGp * gp, and the combine's factors for R, S, V, G.
+constexpr float kVGp = kVNewton ? -4.f : -1.f;
+constexpr float kVScaleR = kVNewton ? 0.03125f : -1.f;
+constexpr float kVScaleS = kVNewton ? -0.125f : 1.f;
+constexpr float kVScaleV = kVNewton ? 0.125f : -1.f;
+constexpr float kVScaleG = kVNewton ? 0.125f : -1.f;
+
 // One j-particle of the VJP pass, 64 bytes, each value duplicated for packed
-// FP32x2 use: (-x, -y, -z, m, ga_x, ga_y, ga_z, -4 gp).
+// FP32x2 use: (-x, -y, -z, m, ga_x, ga_y, ga_z, h = kVGp gp).
 struct alignas(64) VPart {
     float2 nx, ny, nz, m, gx, gy, gz, gp4n;
 };
@@ -51,7 +65,7 @@ __global__ void vjp_pack_kernel(const float *__restrict__ x, const float *__rest
         v[4] = ga[3 * i];
         v[5] = ga[3 * i + 1];
         v[6] = ga[3 * i + 2];
-        v[7] = -4.f * gp[i];
+        v[7] = kVGp * gp[i];
     }
     float4 *dst = reinterpret_cast<float4 *>(vp + i);
 #pragma unroll
@@ -96,7 +110,7 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
             s = fma2(dy, dy, s);
             s = fma2(dz, dz, s);
             const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
-            float2 u = mul2(y, fma2(s, mul2(y, y), m3));  // u = -2 y1
+            float2 u = kVNewton ? mul2(y, fma2(s, mul2(y, y), m3)) : y;  // -2 y1, or y
             if (DIAG) {
                 if (jj == self0[q]) u.x = 0.f;
                 if (jj == self1[q]) u.y = 0.f;
@@ -204,7 +218,7 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
                     e[h][4] = 3.f * V.gy.x;
                     e[h][5] = 3.f * V.gz.x;
                     e[h][6] = -3.f * V.m.x;
-                    e[h][7] = -V.gp4n.x;  // 4 gp_i
+                    e[h][7] = -V.gp4n.x;  // h_i' = -h_i
                     e[h][8] = -V.m.x;
                 }
                 xi[q] = make_float2(e[0][0], e[1][0]);
@@ -284,14 +298,14 @@ __global__ void vjp_combine_kernel(const VjpArgs A, int ib, float *__restrict__ 
         for (int r = 0; r < 8; ++r) s[r] = __fadd_rn(s[r], v[r]);
     }
     const float mi = A.m[i];
-    // gx = R/32 - ga_i S/8 + m_i V/8
+    // gx = kVScaleR R + kVScaleS ga_i S + kVScaleV m_i V
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float gai = A.ga[3 * i + c];
-        const float t = __fmaf_rn(mi, 0.125f * s[4 + c], -(gai * (0.125f * s[3])));
-        gx[3 * i + c] = __fadd_rn(0.03125f * s[c], t);
+        const float t = __fmaf_rn(mi, kVScaleV * s[4 + c], gai * (kVScaleS * s[3]));
+        gx[3 * i + c] = __fadd_rn(kVScaleR * s[c], t);
     }
-    gm[i] = 0.125f * s[7];
+    gm[i] = kVScaleG * s[7];
 }
 
 }  // namespace nbk

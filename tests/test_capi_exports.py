@@ -49,6 +49,19 @@ def test_host_only_calls(lib):
         assert t.ipt % 2 == 0 and 3072 % ib == 0 and 3072 % t.jtile == 0 and t.stages >= 2
         assert t.threads % 32 == 0 and t.release in (0, 1) and t.unroll >= 1
         assert (t.jtile * 32) % 16 == 0
+        assert t.refine in (0, 1)
+    # Both arithmetic forms are compiled in each mode: the special-function
+    # unit's rsqrt as is (the built-in default) and with one Newton step.
+    for mode in (lib.NB_PLAIN, lib.NB_COMPENSATED):
+        assert {t.refine for t in lib.nb_list_tiles(mode)} == {0, 1}
+
+
+def test_tile_struct_matches_header(lib):
+    # The binding's nb_tile has the C struct's fields, in order.
+    src = open(HEADER).read()
+    body = re.search(r"typedef struct nb_tile \{(.*?)\} nb_tile;", src, re.S).group(1)
+    fields = re.findall(r"int (\w+);", body)
+    assert [f for f, _ in lib.nb_tile._fields_] == fields
 
 
 def test_create_reports_error_without_gpu(lib):

@@ -108,6 +108,37 @@ def test_every_tile_shape(nb, ctx, oracle_mod, mode):
         nb.nb_set_tile(ctx, mode, None)
 
 
+def test_default_shapes_skip_newton_step(nb, ctx):
+    # The built-in shapes use the special-function unit's rsqrt without the
+    # Newton step (13 FP32 ops per pair); the step's shapes stay selectable.
+    for mode in (0, 1):
+        for n in (1000, 10000, 100000, 1 << 20):
+            assert nb.nb_get_tile(ctx, n, mode).refine == 0, (mode, n)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_newton_step_matches_unrefined_accuracy(nb, ctx, oracle_mod, mode):
+    # The same shape with and without the Newton step: both within the
+    # mode's tolerance, and the step does not make the result more accurate
+    # than the special-function unit's estimate by more than a factor 2.
+    n = 12000
+    x32, m32 = plummer32(n, seed=17)
+    eps = np.float32(1.0 / 128)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    errs = {}
+    try:
+        for refine in (0, 1):
+            base = [t for t in nb.nb_list_tiles(mode) if t.refine == refine][0].as_tuple()
+            nb.nb_set_tile(ctx, mode, base)
+            a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+            ea, ep = rel_errors(a, p, ra, rp, ramag)
+            assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode], (base, ea.max(), ep.max())
+            errs[refine] = (ea.max(), ep.max())
+    finally:
+        nb.nb_set_tile(ctx, mode, None)
+    assert errs[0][0] <= 2 * errs[1][0] and errs[0][1] <= 2 * errs[1][1], errs
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_bitwise_repeatable(nb, ctx, mode):
     x32, m32 = plummer32(20000, seed=3)

@@ -150,7 +150,7 @@ def test_autograd_function_matches_kernel(nb, ctx):
     assert mt.grad.cpu().numpy().tobytes() == gm.tobytes()
 
 
-def _trajectory_grad_check(nb, ctx, oracle_mod, n, eps, dt, steps, ncoords, seed):
+def _trajectory_grad_check(nb, ctx, oracle_mod, n, eps, dt, steps, ncoords, seed, mode=0):
     """Gradients of L = sum |x(T) - y|^2 through `steps` KDK steps with
     checkpoints every 8 steps, from the adjoint kernel, against (1) the FP64
     reverse-mode adjoint of the oracle's trajectory for every coordinate and
@@ -169,7 +169,7 @@ def _trajectory_grad_check(nb, ctx, oracle_mod, n, eps, dt, steps, ncoords, seed
     vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
     mt = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
     yt = torch.from_numpy(y).to(dev)
-    xT, _ = leapfrog(xt, vt, mt, eps, dt, steps, checkpoint_every=8, nbctx=ctx)
+    xT, _ = leapfrog(xt, vt, mt, eps, dt, steps, checkpoint_every=8, mode=mode, nbctx=ctx)
     loss = ((xT - yt) ** 2).sum()
     loss.backward()
     grads = {"x": xt.grad.cpu().numpy(), "v": vt.grad.cpu().numpy(),
@@ -226,6 +226,62 @@ def test_trajectory_gradient_small(nb, ctx, oracle_mod):
     _trajectory_grad_check(nb, ctx, oracle_mod, 512, np.float32(1.0 / 64), 1.0 / 512, 64, 15, 4)
 
 
+def test_trajectory_gradient_small_compensated(nb, ctx, oracle_mod):
+    # The same with the compensated force (per-tile reference frames in the
+    # forward and in the adjoint's replay).
+    _trajectory_grad_check(nb, ctx, oracle_mod, 512, np.float32(1.0 / 64), 1.0 / 512, 64, 6, 5,
+                           mode=1)
+
+
+def _autograd_composition(x0, v0, m, eps, dt, steps, ctx):
+    """The trajectory built from NBForce and PyTorch arithmetic (the kicks and
+    drift written as tensor operations), differentiated by autograd."""
+    import torch
+    from paper_0904_3659_gb300.autograd import NBForce
+    a, _ = NBForce.apply(x0.float(), m, eps, 0, ctx)
+    x, v = x0, v0
+    for _ in range(steps):
+        v = v + (0.5 * dt) * (-a.double())
+        x = x + dt * v
+        a, _ = NBForce.apply(x.float(), m, eps, 0, ctx)
+        v = v + (0.5 * dt) * (-a.double())
+    return x, v
+
+
+@pytest.mark.parametrize("every", [4, 0])
+def test_library_adjoint_matches_autograd_composition(nb, ctx, every):
+    # The library's replay + reverse sweep against autograd through the same
+    # forward arithmetic (plain mode: the leap-frog kernels feed the pair
+    # kernel FP32 positions exactly as NBForce does; the kernels' FP64 drift
+    # may fuse x + dt v into one rounding where PyTorch rounds twice, so the
+    # trajectories agree to FP64 rounding). The gradients differ only in the
+    # order and precision of their accumulations (the library adds the mass
+    # gradient in FP64).
+    import torch
+    from paper_0904_3659_gb300.autograd import leapfrog
+    dev = torch.device("cuda:0")
+    x0, v0, m = workloads.plummer(2500, seed=21)
+    y = torch.from_numpy(workloads.targets(x0, seed=22)).to(dev)
+    eps, dt, steps = np.float32(1.0 / 64), 1.0 / 512, 10
+    res = []
+    for which in ("library", "autograd"):
+        xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
+        vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
+        mt = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
+        if which == "library":
+            xT, vT = leapfrog(xt, vt, mt, eps, dt, steps, checkpoint_every=every, nbctx=ctx)
+        else:
+            xT, vT = _autograd_composition(xt, vt, mt, eps, dt, steps, ctx)
+        (((xT - y) ** 2).sum() + 0.5 * (vT ** 2).sum()).backward()
+        res.append((xT.detach().cpu().numpy(), xt.grad.cpu().numpy(), vt.grad.cpu().numpy(),
+                    mt.grad.cpu().numpy()))
+    (xl, gxl, gvl, gml), (xa, gxa, gva, gma) = res
+    np.testing.assert_allclose(xl, xa, rtol=1e-13, atol=1e-15)
+    for u, w in ((gxl, gxa), (gvl, gva)):
+        np.testing.assert_allclose(u, w, rtol=1e-5, atol=1e-7 * np.abs(w).max())
+    np.testing.assert_allclose(gml, gma, rtol=1e-4, atol=1e-5 * np.abs(gma).max())
+
+
 def test_trajectory_gradient_plummer16384(nb, ctx, oracle_mod):
     # The full workload (N = 16384, eps = 1/64, 64 steps of dt = 1/512,
     # checkpoints every 8): each FP64 oracle trajectory takes seconds, so 3
@@ -250,8 +306,8 @@ def test_checkpointing_does_not_change_gradients(nb, ctx):
                           nbctx=ctx)
         (xT.square().sum() + vT.square().sum()).backward()
         out.append((xt.grad.cpu().numpy(), vt.grad.cpu().numpy(), mt.grad.cpu().numpy()))
-    # Recomputed segments give the same values; only the order in which
-    # autograd adds gradient contributions may differ.
+    # Recomputed segments give the same positions and the reverse sweep adds
+    # the contributions in the same order whatever the segment length.
     for o in out[1:]:
         for u, w in zip(out[0], o):
-            np.testing.assert_allclose(w, u, rtol=1e-12, atol=1e-14)
+            assert u.tobytes() == w.tobytes()
