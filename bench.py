@@ -306,6 +306,52 @@ def extra_batched(nb, ctx, dev, torch, plain_rate):
             "kdk32_gint_s": pairs * steps / (ms_lf * 1e-3) / 1e9}
 
 
+def extra_single_call(nb, ctx, dev, torch):
+    """N = 4096 Plummer, eps = 0.01: one nb_force call (pack, pair kernel,
+    combine), launched directly and replayed from a captured CUDA graph. The
+    results are returned under "_results" for the oracle comparison of the
+    cpu_baseline leg."""
+    w = workloads.WORKLOADS["plummer4096"]
+    n, eps = w["n"], np.float32(w["eps"])
+    x0, _, m = workloads.plummer(n, seed=w["seed"])
+    x32, m32 = x0.astype(np.float32), m.astype(np.float32)
+    x = torch.from_numpy(x32).to(dev)
+    mt = torch.from_numpy(m32).to(dev)
+    a = torch.empty((n, 3), device=dev)
+    p = torch.empty(n, device=dev)
+    out = {"workload": "plummer4096", "n": n, "_results": {"x": x32, "m": m32, "eps": eps}}
+    for mode, name in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
+        nb.nb_reserve(ctx, n, mode)                # no allocation inside the capture
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(10):
+                nb.nb_force(ctx, x, mt, n, eps, a, p, mode, side)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            nb.nb_force(ctx, x, mt, n, eps, a, p, mode)
+        reps = 200
+        times = {}
+        for how in ("direct", "graph"):
+            e0, e1 = _events(torch)
+            e0.record()
+            for _ in range(reps):
+                if how == "direct":
+                    nb.nb_force(ctx, x, mt, n, eps, a, p, mode)
+                else:
+                    graph.replay()
+            e1.record()
+            nb.nb_synchronize(ctx)
+            times[how] = e0.elapsed_time(e1) / reps * 1e3
+        out["_results"][name] = (a.cpu().numpy(), p.cpu().numpy())
+        out[name] = {"us_per_call": times["direct"], "us_per_call_graph": times["graph"],
+                     "gint_s": n * n / (times["direct"] * 1e-6) / 1e9,
+                     "gint_s_graph": n * n / (times["graph"] * 1e-6) / 1e9,
+                     "tile": list(nb.nb_get_tile(ctx, n, mode).as_tuple())}
+    return out
+
+
 def extra_adjoint(nb, ctx, dev, torch, plain_rate):
     """N = 16384 Plummer, eps = 1/64: the VJP pair kernel's rate, and one
     64-step differentiable trajectory (forward + backward, checkpoints every 8)."""
@@ -544,7 +590,8 @@ def run_ours(args):
                               "speedup_without_step": n_ms / ms_plain}
     if args.extras:
         plain_rate = value / world / 1e9
-        for key, fn in (("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch)),
+        for key, fn in (("single_call", lambda: extra_single_call(nb, ctx, dev, torch)),
+                        ("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch)),
                         ("batched", lambda: extra_batched(nb, ctx, dev, torch, plain_rate)),
                         ("adjoint", lambda: extra_adjoint(nb, ctx, dev, torch, plain_rate))):
             try:
@@ -564,6 +611,13 @@ def run_ours(args):
                                "compensated": oracle_errors(a_comp[rows], p_comp[rows], ref)}
         if newton is not None:
             out["newton_step"]["oracle_error"] = oracle_errors(newton[2][rows], newton[3][rows], ref)
+        single = out.get("single_call", {}).get("_results")
+        if single is not None:
+            import oracle
+            ref4 = oracle.force(single["x"], single["m"], single["eps"])
+            for name in ("plain", "compensated"):
+                out["single_call"][name]["oracle_error_all_rows"] = oracle_errors(*single[name], ref4)
+    out.get("single_call", {}).pop("_results", None)
     print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
