@@ -91,7 +91,16 @@ typedef struct nb_ctx nb_ctx;
  * parities; the PTX ISA gives the same bound for the whole range), and one
  * Newton step evaluated in FP32 does not lower that bound (its own three
  * roundings are of the same size), so both settings meet the same error
- * targets. A tile passed with fewer fields (zero-filled) means refine = 0. */
+ * targets. A tile passed with fewer fields (zero-filled) means refine = 0.
+ * `fused` = 1 marks a single-launch shape for small n: each CTA of `threads`
+ * threads takes one i-block of 32 * `ipt` particles (every warp holds the
+ * same i) and one j-chunk, which its threads load from x and m into shared
+ * memory themselves (no pack kernel, no TMA; `stages` = 1); warp w sums the
+ * `jtile`-particle tiles w, w + warps, ... and the warps' sums are added in
+ * warp order. The last CTA of an i-block to finish adds the chunks' partial
+ * sums in chunk order and writes its a, p (no combine kernel). Callers that
+ * pass packed FP64 state (the leap-frog) use the non-fused shape of the same
+ * size class instead. */
 typedef struct nb_tile {
     int threads;
     int ipt;
@@ -103,6 +112,7 @@ typedef struct nb_tile {
     int sums_in_smem;
     int packed;
     int refine;
+    int fused;
 } nb_tile;
 
 /* Create a context on CUDA device `device`. *out receives the handle. */

@@ -55,7 +55,8 @@ class nb_tile(ctypes.Structure):
                 ("jtile", ctypes.c_int), ("stages", ctypes.c_int),
                 ("unroll", ctypes.c_int), ("minblocks", ctypes.c_int),
                 ("release", ctypes.c_int), ("sums_in_smem", ctypes.c_int),
-                ("packed", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("packed", ctypes.c_int), ("refine", ctypes.c_int),
+                ("fused", ctypes.c_int)]
 
     def as_tuple(self):
         return tuple(getattr(self, f) for f, _ in self._fields_)

@@ -40,6 +40,8 @@ struct nb_ctx {
     size_t jp_bytes = 0;
     void *d_partial = nullptr;
     size_t partial_bytes = 0;
+    int *d_count = nullptr;  // fused shapes: arrivals per i-block, zero between launches
+    int64_t count_cap = 0;
     // device staging for nb_force_host
     float *d_hx = nullptr, *d_hm = nullptr, *d_ha = nullptr, *d_hp = nullptr;
     int64_t host_cap = 0;
@@ -146,6 +148,29 @@ cudaError_t ensure_buffer(void **ptr, size_t *cap, size_t bytes) {
     return cudaSuccess;
 }
 
+// Arrival counters of the fused shapes: zeroed when allocated; every launch
+// leaves them zero again (the last CTA of each i-block resets its count).
+cudaError_t ensure_counters(nb_ctx *ctx, int64_t nib) {
+    if (nib <= ctx->count_cap && ctx->d_count) return cudaSuccess;
+    if (ctx->d_count) {
+        cudaError_t e = cudaFree(ctx->d_count);
+        ctx->d_count = nullptr;
+        ctx->count_cap = 0;
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t want = std::max<int64_t>(nib, 1024);
+    cudaError_t e = cudaMalloc(&ctx->d_count, (size_t)want * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_count, 0, (size_t)want * sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(ctx->d_count);
+        ctx->d_count = nullptr;
+        return e;
+    }
+    ctx->count_cap = want;
+    return cudaSuccess;
+}
+
 int resident_ctas(nb_ctx *ctx, const PairVariant &v) {
     auto it = ctx->occupancy.find(v.kernel);
     if (it != ctx->occupancy.end()) return it->second * ctx->sm_count;
@@ -174,9 +199,45 @@ const PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp) {
 // (already packed); else x, m are packed into the context's buffer.
 nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *prepacked,
                     int64_t n, float eps, float *a, float *p, bool comp, cudaStream_t st) {
-    const PairVariant &v = choose_variant(ctx, n, comp);
+    const PairVariant *vp = &choose_variant(ctx, n, comp);
+    // Packed input (FP64 state packed by the caller): a shape that reads it.
+    if (prepacked && vp->tile.fused) vp = pair_variant(comp, pair_default_unfused_index(comp, n));
+    const PairVariant &v = *vp;
     const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
     cudaError_t e;
+    if (v.tile.fused) {
+        e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, plan.partial_bytes);
+        if (e == cudaSuccess) e = ensure_counters(ctx, plan.nib);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (partial sums)");
+        PairArgs fa{};
+        fa.partial = static_cast<float4 *>(ctx->d_partial);
+        fa.err = ctx->d_err;
+        fa.njt = plan.njt;
+        fa.units = plan.units;
+        fa.grid = plan.grid;
+        fa.maxseg = plan.maxseg;
+        fa.eps2 = eps * eps;
+        fa.fault_unit = -1;
+        fa.wait_ns = ctx->wait_ns;
+        fa.npad = plan.npad;
+        fa.partial_len = (int64_t)(ctx->partial_bytes / sizeof(float4));
+        fa.x = x;
+        fa.m = m;
+        fa.n = n;
+        fa.a = a;
+        fa.p = p;
+        fa.counters = ctx->d_count;
+        fa.nib = plan.nib;
+        fa.nchunks = plan.nchunks;
+        fa.a_scale = accel_scale(v.tile.refine);
+        fa.p_scale = pot_scale(v.tile.refine);
+        {
+            TimedLaunch t(ctx, K_PAIR, st);
+            e = v.launch(fa, plan.grid, v.smem, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fused pair kernel launch");
+        return NB_OK;
+    }
     const JPart *jp = prepacked;
     if (!jp) {
         e = ensure_buffer(&ctx->d_jp, &ctx->jp_bytes, (size_t)plan.npad * sizeof(JPart));
@@ -359,6 +420,7 @@ void nb_destroy(nb_ctx *ctx) {
     nbx::ext_release(ctx->ext);
     cudaFree(ctx->d_jp);
     cudaFree(ctx->d_partial);
+    cudaFree(ctx->d_count);
     cudaFree(ctx->d_hx);
     cudaFree(ctx->d_hm);
     cudaFree(ctx->d_ha);
@@ -392,15 +454,18 @@ nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode) {
     DeviceGuard g(ctx->device);
     const bool comp = mode == NB_COMPENSATED;
     size_t jp = 0, part = 0;
+    int64_t nib = 0;
     // Every shape this context might pick for n: reserve for the largest.
     for (int k = 0; k < pair_variant_count(comp); ++k) {
         const PairVariant &v = *pair_variant(comp, k);
         const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
         jp = std::max(jp, (size_t)plan.npad * sizeof(JPart));
         part = std::max(part, plan.partial_bytes);
+        if (v.tile.fused) nib = std::max(nib, plan.nib);
     }
     cudaError_t e = ensure_buffer(&ctx->d_jp, &ctx->jp_bytes, jp);
     if (e == cudaSuccess) e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, part);
+    if (e == cudaSuccess && nib > 0) e = ensure_counters(ctx, nib);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "nb_reserve");
     return NB_OK;
 }

@@ -95,8 +95,8 @@ __device__ __forceinline__ bool nb_in(int *err, int site, bool cond) {
 #define NB_IN(err, site, cond) true
 #endif
 
-// Reciprocal square root on the special-function unit (approximate; one
-// Newton-Raphson step is applied by the caller).
+// Reciprocal square root on the special-function unit (within 2^-22.9
+// relative on sm_103a; the caller may refine it with a Newton-Raphson step).
 __device__ __forceinline__ float rsqrt_sfu(float s) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(s));

@@ -43,6 +43,17 @@ struct PairArgs {
     const float4 *cref;    // per-j-tile reference points (frame variants only)
     int64_t npad;          // entries of jp (bounds checks of the debug build)
     int64_t partial_len;   // float4 entries of partial (debug build)
+    // Fused variants only: they read x, m themselves and the last CTA to
+    // finish an i-block writes its a, p (no pack or combine kernel).
+    const float *x;        // [n][3]
+    const float *m;        // [n]
+    int64_t n;
+    float *a;              // [n][3]
+    float *p;              // [n]
+    int *counters;         // [nib] arrivals per i-block; zero between launches
+    int64_t nib;
+    int64_t nchunks;       // j-chunks (CTAs) per i-block
+    float a_scale, p_scale;
 };
 
 // Arguments of the deterministic cross-CTA combine.
@@ -66,7 +77,8 @@ struct ReduceArgs {
 inline bool same_tile(const nb_tile &a, const nb_tile &b) {
     return a.threads == b.threads && a.ipt == b.ipt && a.jtile == b.jtile && a.stages == b.stages &&
            a.unroll == b.unroll && a.minblocks == b.minblocks && a.release == b.release &&
-           a.sums_in_smem == b.sums_in_smem && a.packed == b.packed && a.refine == b.refine;
+           a.sums_in_smem == b.sums_in_smem && a.packed == b.packed && a.refine == b.refine &&
+           a.fused == b.fused;
 }
 
 // Factors that turn the pair kernels' sums into a_i and p_i (exact powers of
@@ -97,6 +109,9 @@ int pair_variant_count(bool comp);
 const PairVariant *pair_variant(bool comp, int idx);
 const PairVariant *pair_variant_find(bool comp, const nb_tile &t);
 int pair_default_index(bool comp, int64_t n);
+// The built-in shape for n among those that read packed particles (not
+// fused), for callers that pack themselves (leap-frog from FP64 state).
+int pair_default_unfused_index(bool comp, int64_t n);
 
 // Launchers (nb_pair.cu).
 cudaError_t launch_pack_f32(const float *x, const float *m, int64_t n, int64_t npad, JPart *jp,
@@ -106,7 +121,7 @@ cudaError_t launch_fill_uniform(float *x, float *m, int64_t n, uint64_t seed, cu
 
 // Work decomposition of one nb_force call for a given variant.
 struct PairPlan {
-    int64_t n, npad, nib, njt, units;
+    int64_t n, npad, nib, njt, units, nchunks;
     int grid, maxseg, ib, words;
     size_t partial_bytes;
     int64_t partial_len() const { return (int64_t)(partial_bytes / sizeof(float4)); }

@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "nb_combine.cuh"
 #include "nb_device.cuh"
 #include "nb_internal.h"
 #include "nb_tile.cuh"
@@ -328,35 +329,6 @@ __global__ void __launch_bounds__(THREADS, MINB) pair_kernel(const PairArgs args
 // ---------------------------------------------------------------------------
 // Combine: for each i, add the partials of its i-block in CTA order and
 // remove the factors the pair kernel's sums carry (r.a_scale, r.p_scale).
-__device__ __forceinline__ int64_t cta_of_unit(int64_t u, int64_t units, int grid) {
-    return ((u + 1) * (int64_t)grid - 1) / units;
-}
-
-__global__ void reduce_plain_kernel(const ReduceArgs r) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= r.n) return;
-    const int64_t b = i / r.ib, w = i - b * r.ib;
-    const int64_t clo = cta_of_unit(b * r.njt, r.units, r.grid);
-    const int64_t chi = cta_of_unit(b * r.njt + r.njt - 1, r.units, r.grid);
-    float ax = 0.f, ay = 0.f, az = 0.f, pp = 0.f;
-    for (int64_t c = clo; c <= chi; ++c) {
-        const int64_t bf = (c * r.units / r.grid) / r.njt;
-        const int64_t idx = (c * r.maxseg + (b - bf)) * r.ib + w;
-        if (!NB_IN(r.err, 5, b - bf >= 0 && b - bf < r.maxseg && idx < r.partial_len)) continue;
-        const float4 v = r.partial[idx];
-        ax = __fadd_rn(ax, v.x);
-        ay = __fadd_rn(ay, v.y);
-        az = __fadd_rn(az, v.z);
-        pp = __fadd_rn(pp, v.w);
-    }
-    const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
-    if (!NB_IN(r.err, 6, o >= 0 && o < r.n)) return;
-    r.a[3 * o + 0] = r.a_scale * ax;
-    r.a[3 * o + 1] = r.a_scale * ay;
-    r.a[3 * o + 2] = r.a_scale * az;
-    r.p[o] = r.p_scale * pp;
-}
-
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
@@ -365,36 +337,248 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-__global__ void reduce_comp_kernel(const ReduceArgs r) {
+// Sum, in CTA order, the partials of slot w of i-block b written by CTAs
+// clo..chi (layout [cta][maxseg][W][ib] float4, W = 2 with Kahan carries).
+// Plain: S += hi. Compensated: TwoSum of the segment values into (S, E).
+// The loads of up to 8 segments are issued together (L2 latency, not
+// bandwidth, bounds a combine with many segments); the additions keep the
+// CTA order, so the result does not depend on the batching. Each CTA's
+// segment is located with SegWalk (no 64-bit division per segment).
+template <bool COMP>
+__device__ __forceinline__ void sum_segments(const float4 *__restrict__ partial, int64_t partial_len,
+                                             int *err, int64_t b, int64_t w, int64_t clo, int64_t chi,
+                                             int64_t units, int grid, int64_t njt, int maxseg,
+                                             int64_t ib, float (&S)[4], float (&E)[4]) {
+    constexpr int K = 8;
+    constexpr int W = COMP ? 2 : 1;
+    SegWalk sw(clo, units, grid, njt);
+    for (int64_t c0 = clo; c0 <= chi; c0 += K) {
+        float4 hi[K], lo[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t cc = c0 + k;
+            hi[k] = lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (cc > chi) continue;
+            if (cc > clo) sw.next();
+            const int64_t bf = sw.bf;
+            const int64_t base = (cc * maxseg + (b - bf)) * W * ib + w;
+            if (!NB_IN(err, 5, b - bf >= 0 && b - bf < maxseg && base + (W - 1) * ib < partial_len))
+                continue;  // (debug build) recorded; the slot adds zero
+            hi[k] = __ldcg(partial + base);
+            if (COMP) lo[k] = __ldcg(partial + base + ib);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (c0 + k > chi) break;
+            const float h[4] = {hi[k].x, hi[k].y, hi[k].z, hi[k].w};
+            const float l[4] = {lo[k].x, lo[k].y, lo[k].z, lo[k].w};
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                if (COMP) {
+                    float t, e;
+                    two_sum(S[qq], h[qq], t, e);
+                    S[qq] = t;
+                    E[qq] = __fadd_rn(E[qq], __fsub_rn(e, l[qq]));  // segment value = hi - lo
+                } else {
+                    S[qq] = __fadd_rn(S[qq], h[qq]);
+                }
+            }
+        }
+    }
+}
+
+template <bool COMP>
+__global__ void reduce_kernel(const ReduceArgs r) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= r.n) return;
     const int64_t b = i / r.ib, w = i - b * r.ib;
     const int64_t clo = cta_of_unit(b * r.njt, r.units, r.grid);
     const int64_t chi = cta_of_unit(b * r.njt + r.njt - 1, r.units, r.grid);
     float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t c = clo; c <= chi; ++c) {
-        const int64_t bf = (c * r.units / r.grid) / r.njt;
-        const int64_t base = (c * r.maxseg + (b - bf)) * 2 * r.ib + w;
-        if (!NB_IN(r.err, 5, b - bf >= 0 && b - bf < r.maxseg && base + r.ib < r.partial_len))
-            continue;
-        const float4 hi = r.partial[base];
-        const float4 lo = r.partial[base + r.ib];
-        const float h[4] = {hi.x, hi.y, hi.z, hi.w};
-        const float l[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float s, e;
-            two_sum(S[q], h[q], s, e);
-            S[q] = s;
-            E[q] = __fadd_rn(E[q], __fsub_rn(e, l[q]));  // segment value = hi - lo
-        }
-    }
+    sum_segments<COMP>(r.partial, r.partial_len, r.err, b, w, clo, chi, r.units, r.grid, r.njt,
+                       r.maxseg, r.ib, S, E);
     const int64_t o = r.perm ? (int64_t)r.perm[i] : i;
     if (!NB_IN(r.err, 6, o >= 0 && o < r.n)) return;
     r.a[3 * o + 0] = r.a_scale * __fadd_rn(S[0], E[0]);
     r.a[3 * o + 1] = r.a_scale * __fadd_rn(S[1], E[1]);
     r.a[3 * o + 2] = r.a_scale * __fadd_rn(S[2], E[2]);
     r.p[o] = r.p_scale * __fadd_rn(S[3], E[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Fused single-launch variant for small n (tile field fused = 1). Work unit:
+// (i-block b of IB = 32 IPT particles, j-chunk c of nchunks), one CTA each.
+//  * The CTA's WARPS warps all hold the same i-particles (each lane IPT/2
+//    packed pairs) and split the chunk's j-range: warp w sums the JT-particle
+//    tiles w, w + WARPS, ... of each shared-memory block. The threads load
+//    and pack each block of up to JMAX particles from x, m themselves (no
+//    pack kernel, no TMA).
+//  * The warps' sums are added in warp order through shared memory, giving
+//    the CTA's partial for the i-block; the last of the i-block's nchunks
+//    CTAs to arrive (a count per i-block, reset by that CTA) adds the chunk
+//    partials in chunk order and writes a_i, p_i (no combine kernel).
+// Every addition order is fixed by the launch shape, so results are
+// bit-reproducible; there are no waits on other CTAs.
+constexpr int kFusedJmax = 1024;  // particles per shared-memory block (32 KB)
+
+template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
+__global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const PairArgs args) {
+    static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
+    static_assert(kFusedJmax % JT == 0, "blocks hold whole tiles");
+    constexpr int THREADS = WARPS * 32;
+    constexpr int P = IPT / 2;
+    constexpr int IB = 32 * IPT;
+    constexpr int W = COMP ? 2 : 1;  // float4 words per i in a partial
+    constexpr int TPB = kFusedJmax / JT;
+    static_assert(kPad % IB == 0, "i-blocks must divide the padding");
+    static_assert(WARPS * W * IB * sizeof(float4) <= kFusedJmax * sizeof(JPart),
+                  "the cross-warp sums reuse the particle block");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    JPart *blk = reinterpret_cast<JPart *>(smem);
+    float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after the last block
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = args.n, nch = args.nchunks;
+    const int64_t b = blockIdx.x / nch, c = blockIdx.x - b * nch;
+    const int64_t t0 = c * args.njt / nch, t1 = (c + 1) * args.njt / nch;  // chunk's tiles
+
+    float2 xi[P], yi[P], zi[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int64_t i0 = b * IB + (2 * q) * 32 + lane, i1 = i0 + 32;
+        float3 p0 = make_float3(0.f, 0.f, 0.f), p1 = p0;
+        if (i0 < n) p0 = make_float3(args.x[3 * i0], args.x[3 * i0 + 1], args.x[3 * i0 + 2]);
+        if (i1 < n) p1 = make_float3(args.x[3 * i1], args.x[3 * i1 + 1], args.x[3 * i1 + 2]);
+        xi[q] = make_float2(p0.x, p1.x);
+        yi[q] = make_float2(p0.y, p1.y);
+        zi[q] = make_float2(p0.z, p1.z);
+    }
+    const float2 eps2 = splat2(args.eps2);
+    const float2 zero2 = splat2(0.f);
+    float2 sum[P][4], cmp[P][4];
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) sum[q][r] = cmp[q][r] = zero2;
+
+    for (int64_t bt0 = t0; bt0 < t1; bt0 += TPB) {
+        const int64_t bt1 = bt0 + TPB < t1 ? bt0 + TPB : t1;
+        const int cnt = (int)(bt1 - bt0) * JT;
+        for (int k = tid; k < cnt; k += THREADS) {
+            const int64_t j = bt0 * JT + k;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond n: inert (m = 0 at the origin)
+            if (j < n) v = make_float4(args.x[3 * j], args.x[3 * j + 1], args.x[3 * j + 2], args.m[j]);
+            float4 *dst = reinterpret_cast<float4 *>(blk + k);
+            const float hm = -0.5f * v.w;
+            dst[0] = make_float4(-v.x, -v.x, -v.y, -v.y);
+            dst[1] = make_float4(-v.z, -v.z, hm, hm);
+        }
+        __syncthreads();
+        for (int64_t t = bt0 + warp; t < bt1; t += WARPS) {
+            const JPart *T = blk + (t - bt0) * JT;
+            float2 acc[P][4];
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
+            const int64_t ibase = b * IB, jbase = t * JT;
+            int self0[P], self1[P];
+            if (jbase < ibase + IB && ibase < jbase + JT) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
+                    self1[q] = self0[q] + 32;
+                }
+                tile_pass<P, JT, 1, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+            } else {
+                tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (COMP) {
+                        // Kahan: true value = sum - cmp.
+                        const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
+                        const float2 tt = add2(sum[q][r], y);
+                        cmp[q][r] = add2(add2(tt, neg2(sum[q][r])), neg2(y));
+                        sum[q][r] = tt;
+                    } else {
+                        sum[q][r] = add2(sum[q][r], acc[q][r]);
+                    }
+                }
+        }
+        __syncthreads();  // the block is read by every warp before it is refilled
+    }
+
+    // The warps' sums, added in warp order: the CTA's partial for i-block b.
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int i0 = (2 * q) * 32 + lane, i1 = i0 + 32;
+        float4 *dst = red + (int64_t)warp * W * IB;
+        dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
+        dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+        if (COMP) {
+            dst[IB + i0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
+            dst[IB + i1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
+        }
+    }
+    __syncthreads();
+    const int64_t off = (b * nch + c) * W * (int64_t)IB;
+    for (int l = tid; l < IB; l += THREADS) {
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int w = 0; w < WARPS; ++w) {
+            const float4 hi = red[(int64_t)w * W * IB + l];
+            const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+            if (COMP) {
+                const float4 lo = red[(int64_t)w * W * IB + IB + l];
+                const float lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float t, e;
+                    two_sum(S[r], h[r], t, e);
+                    S[r] = t;
+                    E[r] = __fadd_rn(E[r], __fsub_rn(e, lw[r]));  // warp value = hi - lo
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) S[r] = __fadd_rn(S[r], h[r]);
+            }
+        }
+        if (NB_IN(args.err, 31, off + (W - 1) * IB + l < args.partial_len)) {
+            args.partial[off + l] = make_float4(S[0], S[1], S[2], S[3]);
+            if (COMP) args.partial[off + IB + l] = make_float4(-E[0], -E[1], -E[2], -E[3]);
+        }
+    }
+    __threadfence();  // this CTA's partial is visible before it counts itself in
+    __syncthreads();
+    if (tid == 0) {
+        int last = 0;
+        if (NB_IN(args.err, 32, b >= 0 && b < args.nib)) {
+            const int prev = atomicAdd(&args.counters[b], 1);
+            last = prev == (int)(nch - 1);
+            if (last) atomicExch(&args.counters[b], 0);  // every chunk has arrived
+        }
+        s_last = last;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int l = tid; l < IB; l += THREADS) {
+        const int64_t gi = b * IB + l;
+        if (gi >= n) break;
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+        // Chunk partials of i-block b are CTAs b*nch .. b*nch + nch - 1, one
+        // segment each: the combine's walk over them with units = grid.
+        sum_segments<COMP>(args.partial, args.partial_len, args.err, b, l, b * nch, b * nch + nch - 1,
+                           args.grid, args.grid, nch, 1, IB, S, E);
+        args.a[3 * gi + 0] = args.a_scale * __fadd_rn(S[0], E[0]);
+        args.a[3 * gi + 1] = args.a_scale * __fadd_rn(S[1], E[1]);
+        args.a[3 * gi + 2] = args.a_scale * __fadd_rn(S[2], E[2]);
+        args.p[gi] = args.p_scale * __fadd_rn(S[3], E[3]);
+    }
 }
 
 // Synthetic inputs for tuning runs (timing only; values do not matter
@@ -420,6 +604,12 @@ static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStr
     return cudaGetLastError();
 }
 
+template <int WARPS, int I, int J, int U, int M, bool N, bool C>
+static cudaError_t launch_fused(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
+    fused_kernel<WARPS, I, J, U, M, N, C><<<grid, WARPS * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int T, int I, int J, int S, int A, bool C>
 constexpr size_t pair_smem() {
     // stages, running sums, their barriers, arrival counters, issue records, abort flag
@@ -434,6 +624,13 @@ constexpr size_t pair_smem() {
      (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, (N != 0), C, F>,                      \
      pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, (N != 0), C, F>}
 #define NB_VARIANT(T, I, J, S, U, M, R, A, X, N, C) NB_VARIANT_F(T, I, J, S, U, M, R, A, X, N, C, false)
+// Fused single-launch shapes: T threads (T / 32 warps sharing one i-block of
+// 32 I particles), J-particle warp tiles, one shared-memory block of
+// kFusedJmax particles (stages = 1).
+#define NB_FUSED(T, I, J, U, M, N, C)                                                        \
+    {{T, I, J, 1, U, M, 0, 0, 63, N, 1}, C,                                                     \
+     (const void *)fused_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
+     launch_fused<T / 32, I, J, U, M, (N != 0), C>}
 
 // Plain shapes. The first group evaluates the reciprocal square root without
 // the Newton step (refine 0, 13 FP32 ops per pair); the second keeps the
@@ -467,6 +664,9 @@ static const PairVariant kPlain[] = {
     NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, 1, false),
     NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, 1, false),
     NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, 63, 1, false),
+    NB_FUSED(256, 4, 32, 4, 1, 0, false),
+    NB_FUSED(256, 2, 32, 4, 1, 0, false),
+    NB_FUSED(512, 2, 32, 4, 1, 0, false),
 };
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
@@ -488,6 +688,9 @@ static const PairVariant kComp[] = {
     NB_VARIANT(128, 4, 256, 3, 4, 1, 0, 0, 63, 1, true),
     NB_VARIANT(256, 2, 128, 4, 4, 1, 0, 0, 63, 1, true),
     NB_VARIANT(128, 2, 128, 4, 4, 1, 0, 0, 63, 1, true),
+    NB_FUSED(256, 4, 32, 4, 1, 0, true),
+    NB_FUSED(256, 2, 32, 4, 1, 0, true),
+    NB_FUSED(512, 2, 32, 4, 1, 0, true),
 };
 // Frame variants (compensated, per-tile reference points; jtile must be 256,
 // the only tile length the frames pack is compiled for).
@@ -497,6 +700,7 @@ static const PairVariant kFrames[] = {
 };
 #undef NB_VARIANT
 #undef NB_VARIANT_F
+#undef NB_FUSED
 
 const PairVariant *frames_variant(int64_t n) { return n >= (int64_t)1 << 16 ? &kFrames[0] : &kFrames[1]; }
 
@@ -519,12 +723,12 @@ const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
     return pair_variant(comp, pair_variant_index(comp, t));
 }
 
-// Built-in choices per size class, from the measured shape sweep (GB300,
-// no Newton step): 2 i per thread and 128-particle tiles while the work
-// cannot fill 152 SMs with large i-blocks, then 4 i per thread in 256-thread
-// CTAs; the plain sums from N = 2^17 on take 12 i per thread with the
-// running sums in shared memory.
-int pair_default_index(bool comp, int64_t n) {
+// Built-in packed (not fused) choices per size class, from the measured shape
+// sweep (GB300, no Newton step): 2 i per thread and 128-particle tiles while
+// the work cannot fill 152 SMs with large i-blocks, then 4 i per thread in
+// 256-thread CTAs; the plain sums from N = 2^17 on take 12 i per thread with
+// the running sums in shared memory.
+int pair_default_unfused_index(bool comp, int64_t n) {
     constexpr int R = kDefaultRefine;
     static const nb_tile shapes[2][4] = {
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {64, 4, 128, 4, 4, 1, 0, 0, 63, R},
@@ -541,9 +745,37 @@ int pair_default_index(bool comp, int64_t n) {
     return k >= 0 ? k : 0;  // every default above is compiled; 0 guards a stale edit
 }
 
+// Below kFusedMaxN the single-launch shape wins: at N = 4096 a whole call
+// takes 15 us against 31.5 us for pack + pair + combine, at 8192 about the
+// same as the packed shapes, from 16384 on it is slower (GB300).
+constexpr int64_t kFusedMaxN = (int64_t)1 << 14;
+
+int pair_default_index(bool comp, int64_t n) {
+    if (n >= kFusedMaxN) return pair_default_unfused_index(comp, n);
+    static const nb_tile fused{256, 4, 32, 1, 4, 1, 0, 0, 63, kDefaultRefine, 1};
+    static const int idx[2] = {pair_variant_index(false, fused), pair_variant_index(true, fused)};
+    const int k = idx[comp ? 1 : 0];
+    return k >= 0 ? k : pair_default_unfused_index(comp, n);
+}
+
 PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
     PairPlan p{};
     p.n = n;
+    if (v.tile.fused) {
+        // One CTA per (i-block, j-chunk); as many chunks as fill the GPU once.
+        p.ib = 32 * v.tile.ipt;
+        p.npad = round_up(std::max<int64_t>(n, 1), kPad);
+        p.nib = (n + p.ib - 1) / p.ib;
+        p.njt = (n + v.tile.jtile - 1) / v.tile.jtile;
+        p.nchunks = std::max<int64_t>(1, std::min<int64_t>(p.njt, resident_ctas / std::max<int64_t>(p.nib, 1)));
+        p.units = p.nib * p.nchunks;
+        p.grid = (int)p.units;
+        p.maxseg = 1;
+        p.words = v.comp ? 2 : 1;
+        p.partial_bytes = (size_t)p.grid * p.words * p.ib * sizeof(float4);
+        return p;
+    }
+    p.nchunks = 1;
     p.ib = v.tile.threads * v.tile.ipt;
     p.npad = round_up(std::max<int64_t>(n, 1), kPad);
     p.nib = (n + p.ib - 1) / p.ib;
@@ -571,12 +803,12 @@ cudaError_t launch_pack_f32(const float *x, const float *m, int64_t n, int64_t n
 }
 
 cudaError_t launch_reduce(const ReduceArgs &r, bool comp, cudaStream_t st) {
-    const int threads = 256;
+    const int threads = 64;  // latency-bound: spread small n over many SMs
     const int64_t blocks = (r.n + threads - 1) / threads;
     if (comp)
-        reduce_comp_kernel<<<(unsigned)blocks, threads, 0, st>>>(r);
+        reduce_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(r);
     else
-        reduce_plain_kernel<<<(unsigned)blocks, threads, 0, st>>>(r);
+        reduce_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(r);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "nb_combine.cuh"
 #include "nb_device.cuh"
 #include "nb_ext.h"
 #include "nb_internal.h"
@@ -285,17 +286,33 @@ __global__ void vjp_combine_kernel(const VjpArgs A, int ib, float *__restrict__ 
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     const int64_t b = i / ib, w = i - b * ib;
-    const int64_t clo = ((b * A.njt + 1) * (int64_t)A.grid - 1) / A.units;
-    const int64_t chi = (((b + 1) * A.njt) * (int64_t)A.grid - 1) / A.units;
+    const int64_t clo = cta_of_unit(b * A.njt, A.units, A.grid);
+    const int64_t chi = cta_of_unit(b * A.njt + A.njt - 1, A.units, A.grid);
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int64_t c = clo; c <= chi; ++c) {
-        const int64_t bf = (c * A.units / A.grid) / A.njt;
-        const int64_t base = (c * A.maxseg + (b - bf)) * 2 * ib + w;
-        if (!NB_IN(A.err, 23, b - bf < A.maxseg && base + ib < A.partial_len)) continue;
-        const float4 p0 = A.partial[base], p1 = A.partial[base + ib];
-        const float v[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+    // Loads of up to 8 segments in flight, additions in CTA order.
+    constexpr int K = 8;
+    SegWalk sw(clo, A.units, A.grid, A.njt);
+    for (int64_t c0 = clo; c0 <= chi; c0 += K) {
+        float4 p0[K], p1[K];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) s[r] = __fadd_rn(s[r], v[r]);
+        for (int k = 0; k < K; ++k) {
+            const int64_t c = c0 + k;
+            p0[k] = p1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c > chi) continue;
+            if (c > clo) sw.next();
+            const int64_t bf = sw.bf;
+            const int64_t base = (c * A.maxseg + (b - bf)) * 2 * ib + w;
+            if (!NB_IN(A.err, 23, b - bf < A.maxseg && base + ib < A.partial_len)) continue;
+            p0[k] = __ldcg(A.partial + base);
+            p1[k] = __ldcg(A.partial + base + ib);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (c0 + k > chi) break;
+            const float v[8] = {p0[k].x, p0[k].y, p0[k].z, p0[k].w, p1[k].x, p1[k].y, p1[k].z, p1[k].w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r) s[r] = __fadd_rn(s[r], v[r]);
+        }
     }
     const float mi = A.m[i];
     // gx = kVScaleR R + kVScaleS ga_i S + kVScaleV m_i V
@@ -375,7 +392,7 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
         kernel<<<plan.grid, kVThreads, smem, s>>>(A);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp kernel launch");
-    vjp_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, plan.ib, gx, gm);
+    vjp_combine_kernel<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(A, plan.ib, gx, gm);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp combine launch");
     return NB_OK;
 }

@@ -45,11 +45,13 @@ def test_host_only_calls(lib):
     tiles = lib.nb_list_tiles(lib.NB_PLAIN)
     assert len(tiles) >= 4
     for t in tiles + lib.nb_list_tiles(lib.NB_COMPENSATED):
-        ib = t.threads * t.ipt
-        assert t.ipt % 2 == 0 and 3072 % ib == 0 and 3072 % t.jtile == 0 and t.stages >= 2
+        # i-block: threads * ipt particles (a fused shape: 32 * ipt, shared by its warps)
+        ib = 32 * t.ipt if t.fused else t.threads * t.ipt
+        assert t.ipt % 2 == 0 and 3072 % ib == 0 and 3072 % t.jtile == 0
+        assert t.stages >= (1 if t.fused else 2)
         assert t.threads % 32 == 0 and t.release in (0, 1) and t.unroll >= 1
         assert (t.jtile * 32) % 16 == 0
-        assert t.refine in (0, 1)
+        assert t.refine in (0, 1) and t.fused in (0, 1)
     # Both arithmetic forms are compiled in each mode: the special-function
     # unit's rsqrt as is (the built-in default) and with one Newton step.
     for mode in (lib.NB_PLAIN, lib.NB_COMPENSATED):

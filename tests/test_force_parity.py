@@ -140,6 +140,53 @@ def test_newton_step_matches_unrefined_accuracy(nb, ctx, oracle_mod, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+def test_fused_shapes(nb, ctx, oracle_mod, mode):
+    # Single-launch shapes (no pack or combine kernel; the last CTA of each
+    # i-block adds its partials): sizes run back to back, so a count left
+    # non-zero by one launch would corrupt the next; every call is repeated
+    # and must give the same bits.
+    fused = [t for t in nb.nb_list_tiles(mode) if t.fused]
+    assert fused
+    eps = np.float32(1.0 / 64)
+    cases = []
+    for n in (1, 200, 3001, 9000):
+        x32, m32 = plummer32(n, seed=100 + n)
+        cases.append((n, x32, m32, oracle_mod.force(x32, m32, eps)))
+    try:
+        for tile in fused:
+            nb.nb_set_tile(ctx, mode, tile)
+            for n, x32, m32, (ra, rp, ramag) in cases:
+                a1, p1 = gpu_force(nb, ctx, x32, m32, eps, mode)
+                a2, p2 = gpu_force(nb, ctx, x32, m32, eps, mode)
+                assert a1.tobytes() == a2.tobytes() and p1.tobytes() == p2.tobytes(), (tile, n)
+                ea, ep = rel_errors(a1, p1, ra, rp, ramag)
+                assert ea.max() <= TOL[mode] and ep.max() <= TOL[mode], (tile, n, ea.max(), ep.max())
+    finally:
+        nb.nb_set_tile(ctx, mode, None)
+
+
+def test_fused_override_leaves_leapfrog_on_packed_shapes(nb, ctx):
+    # The leap-frog packs FP64 state itself, so with a fused shape forced it
+    # runs the built-in packed shape of the size class: the same bits.
+    import torch
+    x0, v0, m = workloads.plummer(3000, seed=31)
+    dev = torch.device("cuda:0")
+    runs = []
+    fused = [t for t in nb.nb_list_tiles(0) if t.fused][0]
+    for tile in (None, fused):
+        nb.nb_set_tile(ctx, 0, tile)
+        x = torch.from_numpy(x0.copy()).to(dev)
+        v = torch.from_numpy(v0.copy()).to(dev)
+        mt = torch.from_numpy(m.astype(np.float32)).to(dev)
+        a = torch.empty((3000, 3), dtype=torch.float32, device=dev)
+        nb.nb_leapfrog_step(ctx, x, v, mt, a, None, 3000, np.float32(0.02), 1.0 / 256, 4, 0, 0)
+        nb.nb_synchronize(ctx)
+        runs.append(x.cpu().numpy().tobytes())
+    nb.nb_set_tile(ctx, 0, None)
+    assert runs[0] == runs[1]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 def test_bitwise_repeatable(nb, ctx, mode):
     x32, m32 = plummer32(20000, seed=3)
     a1, p1 = gpu_force(nb, ctx, x32, m32, np.float32(0.01), mode)

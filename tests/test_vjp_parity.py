@@ -251,18 +251,20 @@ def _autograd_composition(x0, v0, m, eps, dt, steps, ctx):
 @pytest.mark.parametrize("every", [4, 0])
 def test_library_adjoint_matches_autograd_composition(nb, ctx, every):
     # The library's replay + reverse sweep against autograd through the same
-    # forward arithmetic (plain mode: the leap-frog kernels feed the pair
-    # kernel FP32 positions exactly as NBForce does; the kernels' FP64 drift
-    # may fuse x + dt v into one rounding where PyTorch rounds twice, so the
-    # trajectories agree to FP64 rounding). The gradients differ only in the
-    # order and precision of their accumulations (the library adds the mass
-    # gradient in FP64).
+    # forward arithmetic (plain mode, one packed tile shape forced for both:
+    # the leap-frog kernels feed the pair kernel FP32 positions exactly as
+    # NBForce does; the kernels' FP64 drift may fuse x + dt v into one
+    # rounding where PyTorch rounds twice, so the trajectories agree to FP64
+    # rounding). The gradients differ only in the order and precision of their
+    # accumulations (the library adds the mass gradient in FP64).
     import torch
     from paper_0904_3659_gb300.autograd import leapfrog
     dev = torch.device("cuda:0")
     x0, v0, m = workloads.plummer(2500, seed=21)
     y = torch.from_numpy(workloads.targets(x0, seed=22)).to(dev)
     eps, dt, steps = np.float32(1.0 / 64), 1.0 / 512, 10
+    packed = [t for t in nb.nb_list_tiles(0) if not t.fused and t.refine == 0][0]
+    nb.nb_set_tile(ctx, 0, packed)
     res = []
     for which in ("library", "autograd"):
         xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
@@ -275,6 +277,7 @@ def test_library_adjoint_matches_autograd_composition(nb, ctx, every):
         (((xT - y) ** 2).sum() + 0.5 * (vT ** 2).sum()).backward()
         res.append((xT.detach().cpu().numpy(), xt.grad.cpu().numpy(), vt.grad.cpu().numpy(),
                     mt.grad.cpu().numpy()))
+    nb.nb_set_tile(ctx, 0, None)
     (xl, gxl, gvl, gml), (xa, gxa, gva, gma) = res
     np.testing.assert_allclose(xl, xa, rtol=1e-13, atol=1e-15)
     for u, w in ((gxl, gxa), (gvl, gva)):
