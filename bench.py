@@ -704,6 +704,8 @@ def run_case(args):
         units = float((cl.sizes.astype(np.float64) ** 2).sum())
     elif case == "vjp":
         n = args.n or 16384
+        if args.tile:
+            nb.nb_set_vjp_tile(ctx, tuple(int(v) for v in args.tile.split(",")))
         x32, m32 = make_inputs(n, 0)
         rng = np.random.default_rng(5)
         x = torch.from_numpy(x32).to(dev)
@@ -739,6 +741,34 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     ctx = nb.Context(0)
     sizes = [int(v) for v in args.sweep_sizes.split(",")]
+    if args.sweep_kind == "vjp":
+        rng = np.random.default_rng(5)
+        for n in sizes:
+            x32, m32 = make_inputs(n, 0)
+            x = torch.from_numpy(x32).to(dev)
+            mt = torch.from_numpy(m32).to(dev)
+            ga = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).to(dev)
+            gp = torch.from_numpy(rng.normal(size=n).astype(np.float32)).to(dev)
+            gx = torch.empty((n, 3), device=dev)
+            gm = torch.empty(n, device=dev)
+            reps = 3 if n >= 1 << 19 else (10 if n >= 1 << 16 else 50)
+            for t in nb.nb_list_vjp_tiles():
+                nb.nb_set_vjp_tile(ctx, t)
+                for _ in range(2):
+                    nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, gp, gx, gm)
+                nb.nb_synchronize(ctx)
+                nb.nb_timing_enable(ctx, True)
+                nb.nb_timing_reset(ctx)
+                for _ in range(reps):
+                    nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, gp, gx, gm)
+                nb.nb_synchronize(ctx)
+                ms, cnt = nb.nb_timing_read(ctx, nb.KERNEL_VJP)
+                nb.nb_timing_enable(ctx, False)
+                print(json.dumps({"n": n, "kernel": "vjp", "tile": list(t.as_tuple()),
+                                  "vjp_ms": ms / cnt,
+                                  "gpair_s": n * n / (ms / cnt * 1e-3) / 1e9}), flush=True)
+            nb.nb_set_vjp_tile(ctx, None)
+        return
     for n in sizes:
         x32, m32 = make_inputs(n, 0)
         x = torch.from_numpy(x32).to(dev)
@@ -791,6 +821,8 @@ def main(argv=None):
     ap.add_argument("--sweep", action="store_true",
                     help="rate of every compiled tile shape over --sweep-sizes (JSON lines)")
     ap.add_argument("--sweep-sizes", default="4096,16384,65536,262144,1048576")
+    ap.add_argument("--sweep-kind", choices=["pair", "vjp"], default="pair",
+                    help="which kernel's compiled shapes --sweep times")
     ap.add_argument("--case", choices=["pair", "comp", "batched", "vjp"], default="",
                     help="time one kernel class at a small size (profiler captures)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",

@@ -263,6 +263,15 @@ nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *
 nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
                        const float *ga, const float *gp, float *gx, float *gm, void *stream);
 
+/* Shape of nb_force_vjp's pair kernel (nb_tile fields threads, ipt, jtile,
+ * stages, unroll, sums_in_smem; the others as listed): force one of the
+ * compiled shapes listed by nb_list_vjp_tiles (NULL restores the built-in
+ * choice), read the shape in use, list the compiled shapes (up to `cap`
+ * written to out, which may be NULL; the total in *count). */
+nb_status nb_set_vjp_tile(nb_ctx *ctx, const nb_tile *tile);
+nb_status nb_get_vjp_tile(nb_ctx *ctx, nb_tile *out);
+nb_status nb_list_vjp_tiles(nb_tile *out, int cap, int *count);
+
 /*
  * nb_force for callers that may not allocate device memory. (This entry
  * point is an engineering addition; the paper has no counterpart.)

@@ -26,7 +26,7 @@ __all__ = [
     "nb_create", "nb_destroy", "nb_last_error", "nb_status_string", "nb_force",
     "nb_force_host", "nb_reserve", "nb_force_batched", "nb_leapfrog_batched_step", "nb_leapfrog_step",
     "nb_leapfrog_adjoint", "nb_energy",
-    "nb_force_vjp", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_set_tuned_tile", "nb_list_tiles",
+    "nb_force_vjp", "nb_set_vjp_tile", "nb_get_vjp_tile", "nb_list_vjp_tiles", "nb_synchronize", "nb_get_tile", "nb_set_tile", "nb_set_tuned_tile", "nb_list_tiles",
     "tune_to_file", "load_tuning",
     "nb_autotune", "nb_timing_enable", "nb_timing_read", "nb_timing_reset",
     "nb_debug_set_fault", "nb_force_noalloc", "force",
@@ -95,6 +95,9 @@ _SIGNATURES = {
                                        _P, _P, _P, _P, _c.c_int, _c.c_int, _P]),
     "nb_energy": (_c.c_int, [_P, _P, _P, _P, _I64, _c.c_float, _P, _c.c_int, _P]),
     "nb_force_vjp": (_c.c_int, [_P, _P, _P, _I64, _c.c_float, _P, _P, _P, _P, _P]),
+    "nb_set_vjp_tile": (_c.c_int, [_P, _c.POINTER(nb_tile)]),
+    "nb_get_vjp_tile": (_c.c_int, [_P, _c.POINTER(nb_tile)]),
+    "nb_list_vjp_tiles": (_c.c_int, [_c.POINTER(nb_tile), _c.c_int, _c.POINTER(_c.c_int)]),
     "nb_synchronize": (_c.c_int, [_P, _P]),
     "nb_get_tile": (_c.c_int, [_P, _I64, _c.c_int, _c.POINTER(nb_tile)]),
     "nb_set_tile": (_c.c_int, [_P, _c.c_int, _c.POINTER(nb_tile)]),
@@ -329,6 +332,31 @@ def load_tuning(ctx, path) -> int:
         except NBError:
             pass
     return applied
+
+
+def nb_set_vjp_tile(ctx, tile) -> None:
+    if tile is None:
+        _check(ctx, library().nb_set_vjp_tile(ctx.handle, None))
+        return
+    if not isinstance(tile, nb_tile):
+        tile = nb_tile(*tile)
+    _check(ctx, library().nb_set_vjp_tile(ctx.handle, ctypes.byref(tile)))
+
+
+def nb_get_vjp_tile(ctx) -> nb_tile:
+    t = nb_tile()
+    _check(ctx, library().nb_get_vjp_tile(ctx.handle, ctypes.byref(t)))
+    return t
+
+
+def nb_list_vjp_tiles() -> list:
+    count = ctypes.c_int(0)
+    st = library().nb_list_vjp_tiles(None, 0, ctypes.byref(count))
+    if st != NB_OK:
+        raise NBError(st, "nb_list_vjp_tiles")
+    arr = (nb_tile * count.value)()
+    library().nb_list_vjp_tiles(arr, count.value, ctypes.byref(count))
+    return [arr[k] for k in range(count.value)]
 
 
 def nb_list_tiles(mode=NB_PLAIN) -> list:

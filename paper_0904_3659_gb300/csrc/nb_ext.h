@@ -34,6 +34,7 @@ struct ExtState {
     static constexpr int kSlots = SLOT_COUNT;
     void *buf[kSlots] = {};
     size_t cap[kSlots] = {};
+    int vjp_idx = -1;  // VJP shape forced by nb_set_vjp_tile (-1: built-in)
 };
 void ext_release(ExtState &s);
 

@@ -18,11 +18,11 @@
 //   R = sum C r,  S = sum m_l u^3,  V = sum u^3 ga_l,  G = sum ((r.ga_l) u^3 + h_l u)
 // where h_i' = -h_i is read back from particle i's own record.
 //  * Without the Newton step (the default): u = y, h_l = -gp_l, so C = -c_il,
-//    G = -gm_i and gx_i = -R + ga_i S - m_i V, gm_i = -G; 30 FP32 operations
-//    per pair.
+//    G = -gm_i and gx_i = -R + ga_i S - m_i V, gm_i = -G; 29 FP32 operations
+//    per pair (C is formed as u^3 (u^2 a + b), without u^5).
 //  * With it: u = -2 y1 (y1 the refined value, as in the force kernel),
 //    h_l = -4 gp_l: y^3 = -u^3/8 and y^5 = -u^5/32 give C = 32 c_il, G = 8 gm_i,
-//    so gx_i = R/32 - ga_i S/8 + m_i V/8, gm_i = G/8; 33 operations.
+//    so gx_i = R/32 - ga_i S/8 + m_i V/8, gm_i = G/8; 32 operations.
 // All scale factors are exact powers of two; one special-function
 // reciprocal square root per pair.
 #include <algorithm>
@@ -118,12 +118,11 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
             }
             const float2 u2 = mul2(u, u);
             const float2 u3 = mul2(u, u2);
-            const float2 u5 = mul2(u3, u2);
             const float2 dgi3 = fma2(dz, g3z[q], fma2(dy, g3y[q], mul2(dx, g3x[q])));  // 3 r.ga_i
             const float2 dgj = fma2(dz, gzj, fma2(dy, gyj, mul2(dx, gxj)));           // r.ga_l
             const float2 a3 = fma2(mj, dgi3, mul2(nm3[q], dgj));
             const float2 b4 = fma2(gp4[q], mj, mul2(nm[q], gp4nj));
-            const float2 c32 = fma2(u5, a3, mul2(u3, b4));
+            const float2 c32 = mul2(u3, fma2(u2, a3, b4));  // u^5 a3 + u^3 b4
             acc[q][0] = fma2(c32, dx, acc[q][0]);
             acc[q][1] = fma2(c32, dy, acc[q][1]);
             acc[q][2] = fma2(c32, dz, acc[q][2]);
@@ -136,7 +135,10 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
     }
 }
 
-template <int THREADS, int IPT, int JT, int STAGES>
+// THREADS, IPT (i per thread, in packed pairs), JT (j-tile), STAGES (TMA
+// stages), UNR (unroll of the j loop), ACCS (running sums in shared memory,
+// one slot per thread, touched once per tile: frees 16 registers per pair).
+template <int THREADS, int IPT, int JT, int STAGES, int UNR, int ACCS>
 __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
     constexpr int P = IPT / 2;
     constexpr int IB = THREADS * IPT;
@@ -145,7 +147,9 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
 
     extern __shared__ __align__(128) unsigned char smem[];
     VPart *tiles = reinterpret_cast<VPart *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES);
+    float2 *ssum = reinterpret_cast<float2 *>(smem + (size_t)STAGES * TILE_BYTES);  // ACCS
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES +
+                                                  (ACCS ? (size_t)P * 8 * THREADS * sizeof(float2) : 0));
 
     const int tid = threadIdx.x;
     const int64_t c = blockIdx.x;
@@ -176,9 +180,13 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
         while (issued < count && issued < STAGES - 1) issue_next();
 
     float2 xi[P], yi[P], zi[P], g3x[P], g3y[P], g3z[P], nm3[P], gp4[P], nm[P];
-    float2 sum[P][8];
+    float2 sum[P][8] = {};  // unused when the running sums live in shared memory
     const float2 eps2 = splat2(args.eps2);
     const float2 zero2 = splat2(0.f);
+    auto get_sum = [&](int q, int r) { return ACCS ? ssum[(q * 8 + r) * THREADS + tid] : sum[q][r]; };
+    auto put_sum = [&](int q, int r, float2 v) {
+        if (ACCS) ssum[(q * 8 + r) * THREADS + tid] = v; else sum[q][r] = v;
+    };
 
     auto flush = [&](int64_t b) {
         const int64_t off = (c * args.maxseg + (b - bfirst)) * 2 * (int64_t)IB;
@@ -187,10 +195,13 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int i0 = (2 * q) * THREADS + tid, i1 = i0 + THREADS;
-            dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
-            dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
-            dst[IB + i0] = make_float4(sum[q][4].x, sum[q][5].x, sum[q][6].x, sum[q][7].x);
-            dst[IB + i1] = make_float4(sum[q][4].y, sum[q][5].y, sum[q][6].y, sum[q][7].y);
+            float2 v[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[r] = get_sum(q, r);
+            dst[i0] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+            dst[i1] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+            dst[IB + i0] = make_float4(v[4].x, v[5].x, v[6].x, v[7].x);
+            dst[IB + i1] = make_float4(v[4].y, v[5].y, v[6].y, v[7].y);
         }
     };
 
@@ -232,7 +243,7 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
                 gp4[q] = make_float2(e[0][7], e[1][7]);
                 nm[q] = make_float2(e[0][8], e[1][8]);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) sum[q][r] = zero2;
+                for (int r = 0; r < 8; ++r) put_sum(q, r, zero2);
             }
         }
         const int s = k % STAGES;
@@ -256,13 +267,13 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
             }
             vjp_tile<P, JT, 1, true>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0, self1);
         } else {
-            vjp_tile<P, JT, 2, false>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
-                                   self1);
+            vjp_tile<P, JT, UNR, false>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
+                                     self1);
         }
 #pragma unroll
         for (int q = 0; q < P; ++q)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) sum[q][r] = add2(sum[q][r], acc[q][r]);
+            for (int r = 0; r < 8; ++r) put_sum(q, r, add2(get_sum(q, r), acc[q][r]));
         if (++jt == args.njt) {
             jt = 0;
             ++b;
@@ -332,8 +343,44 @@ using namespace nbx;
 
 namespace {
 
-constexpr int kVThreads = 128, kVIpt = 4, kVJt = 128, kVStages = 3;
 enum VSlot : int { V_VP = SLOT_VJP_VP, V_PART = SLOT_VJP_PART };
+
+// Compiled VJP shapes (nb_tile fields: threads, ipt, jtile, stages, unroll,
+// sums_in_smem; the others fixed). Entry kVjpDefault is the built-in choice.
+struct VjpVariant {
+    nb_tile tile;
+    const void *kernel;
+    size_t smem;
+    void (*launch)(const VjpArgs &, int grid, size_t smem, cudaStream_t);
+};
+
+template <int T, int I, int J, int S, int U, int A>
+void launch_vjp(const VjpArgs &a, int grid, size_t smem, cudaStream_t st) {
+    vjp_kernel<T, I, J, S, U, A><<<grid, T, smem, st>>>(a);
+}
+
+template <int T, int I, int J, int S, int A>
+constexpr size_t vjp_smem() {
+    return (size_t)S * J * sizeof(VPart) + (A ? (size_t)(I / 2) * 8 * T * sizeof(float2) : 0) +
+           (size_t)S * sizeof(uint64_t);
+}
+
+#define NB_VJP(T, I, J, S, U, A)                                                         \
+    {{T, I, J, S, U, 1, 0, A, 63, kDefaultRefine, 0}, (const void *)vjp_kernel<T, I, J, S, U, A>, \
+     vjp_smem<T, I, J, S, A>(), launch_vjp<T, I, J, S, U, A>}
+const VjpVariant kVjp[] = {
+    NB_VJP(256, 2, 128, 3, 2, 0), NB_VJP(256, 2, 128, 3, 4, 0), NB_VJP(512, 2, 128, 3, 2, 0),
+    NB_VJP(128, 2, 128, 3, 2, 0), NB_VJP(256, 2, 256, 3, 2, 0), NB_VJP(64, 4, 128, 3, 2, 0),
+    NB_VJP(128, 4, 128, 3, 2, 0), NB_VJP(128, 4, 128, 3, 4, 0),
+};
+#undef NB_VJP
+constexpr int kVjpCount = (int)(sizeof(kVjp) / sizeof(kVjp[0]));
+constexpr int kVjpDefault = 0;
+
+const VjpVariant &vjp_variant(nb_ctx *ctx) {
+    const int k = ctx_ext(ctx).vjp_idx;
+    return kVjp[k >= 0 && k < kVjpCount ? k : kVjpDefault];
+}
 
 }  // namespace
 
@@ -348,18 +395,13 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    using K = void (*)(const VjpArgs);
-    const K kernel = vjp_kernel<kVThreads, kVIpt, kVJt, kVStages>;
-    const size_t smem = (size_t)kVStages * kVJt * sizeof(VPart) + kVStages * sizeof(uint64_t);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kernel, kVThreads, smem);
-    cudaGetLastError();
+    const VjpVariant &vv = vjp_variant(ctx);
     PairVariant shape{};
-    shape.tile.threads = kVThreads;
-    shape.tile.ipt = kVIpt;
-    shape.tile.jtile = kVJt;
+    shape.tile = vv.tile;
     shape.comp = true;  // two float4 words per i
-    const PairPlan plan = make_plan(shape, n, std::max(per_sm, 1) * ctx_sm_count(ctx));
+    shape.kernel = vv.kernel;
+    shape.smem = vv.smem;
+    const PairPlan plan = make_plan(shape, n, resident_ctas(ctx, shape));
 
     ExtState &es = ctx_ext(ctx);
     cudaError_t e = ensure_buffer(&es.buf[V_VP], &es.cap[V_VP], (size_t)plan.npad * sizeof(VPart));
@@ -389,10 +431,38 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
     A.partial_len = (int64_t)(es.cap[V_PART] / sizeof(float4));
     {
         TimedLaunch t(ctx, 5, s);
-        kernel<<<plan.grid, kVThreads, smem, s>>>(A);
+        vv.launch(A, plan.grid, vv.smem, s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp kernel launch");
     vjp_combine_kernel<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(A, plan.ib, gx, gm);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp combine launch");
+    return NB_OK;
+}
+
+extern "C" nb_status nb_set_vjp_tile(nb_ctx *ctx, const nb_tile *tile) {
+    if (!ctx) return NB_ERR_ARG;
+    if (!tile) {
+        ctx_ext(ctx).vjp_idx = -1;
+        return NB_OK;
+    }
+    for (int k = 0; k < kVjpCount; ++k)
+        if (same_tile(kVjp[k].tile, *tile)) {
+            ctx_ext(ctx).vjp_idx = k;
+            return NB_OK;
+        }
+    return fail(ctx, NB_ERR_ARG, "tile shape is not one of the compiled VJP shapes");
+}
+
+extern "C" nb_status nb_get_vjp_tile(nb_ctx *ctx, nb_tile *out) {
+    if (!ctx || !out) return NB_ERR_ARG;
+    *out = vjp_variant(ctx).tile;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_list_vjp_tiles(nb_tile *out, int cap, int *count) {
+    if (!count) return NB_ERR_ARG;
+    *count = kVjpCount;
+    if (out)
+        for (int k = 0; k < kVjpCount && k < cap; ++k) out[k] = kVjp[k].tile;
     return NB_OK;
 }

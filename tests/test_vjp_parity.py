@@ -104,6 +104,33 @@ def test_vjp_matches_oracle(nb, ctx, oracle_mod, n):
     assert rel_to_scale(gm, rgm, sm) <= 1e-5
 
 
+def test_every_vjp_shape(nb, ctx, oracle_mod):
+    # Each compiled VJP shape at a size that spans several i-blocks and
+    # j-tiles with a ragged tail, against the FP64 oracle; each repeats bitwise.
+    n = 3001
+    x, _, m = workloads.plummer(n, seed=61)
+    x32, m32 = x.astype(np.float32), m.astype(np.float32)
+    rng = np.random.default_rng(62)
+    ga = rng.normal(size=(n, 3)).astype(np.float32)
+    gp = rng.normal(size=n).astype(np.float32)
+    eps = np.float32(1.0 / 64)
+    rgx, rgm = oracle_mod.force_vjp(x32, m32, eps, ga, gp)
+    sx, sm = vjp_term_scales(x32, m32, eps, ga, gp)
+    tiles = nb.nb_list_vjp_tiles()
+    assert len(tiles) >= 2
+    try:
+        for t in tiles:
+            nb.nb_set_vjp_tile(ctx, t)
+            assert nb.nb_get_vjp_tile(ctx).as_tuple() == t.as_tuple()
+            gx, gm = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
+            gx2, gm2 = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
+            assert gx.tobytes() == gx2.tobytes() and gm.tobytes() == gm2.tobytes(), t
+            assert rel_to_scale(gx, rgx, sx) <= 1e-5, t
+            assert rel_to_scale(gm, rgm, sm) <= 1e-5, t
+    finally:
+        nb.nb_set_vjp_tile(ctx, None)
+
+
 def test_vjp_repeatable_and_dot_product(nb, ctx, oracle_mod):
     # Bit-reproducible; and <J dtheta, w> = <dtheta, J^T w> with J dtheta from
     # a central FP64 difference of the oracle's forward.
