@@ -112,6 +112,8 @@ int pair_default_index(bool comp, int64_t n);
 // The built-in shape for n among those that read packed particles (not
 // fused), for callers that pack themselves (leap-frog from FP64 state).
 int pair_default_unfused_index(bool comp, int64_t n);
+// Whether the tuner times the fused (single-launch, small-n) shapes at n.
+bool fused_candidate(int64_t n);
 
 // Launchers (nb_pair.cu).
 cudaError_t launch_pack_f32(const float *x, const float *m, int64_t n, int64_t npad, JPart *jp,

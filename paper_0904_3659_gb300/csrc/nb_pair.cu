@@ -750,6 +750,8 @@ int pair_default_unfused_index(bool comp, int64_t n) {
 // same as the packed shapes, from 16384 on it is slower (GB300).
 constexpr int64_t kFusedMaxN = (int64_t)1 << 14;
 
+bool fused_candidate(int64_t n) { return n < 2 * kFusedMaxN; }
+
 int pair_default_index(bool comp, int64_t n) {
     if (n >= kFusedMaxN) return pair_default_unfused_index(comp, n);
     static const nb_tile fused{256, 4, 32, 1, 4, 1, 0, 0, 63, kDefaultRefine, 1};
