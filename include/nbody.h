@@ -328,9 +328,8 @@ nb_status nb_list_tiles(nb_mode mode, nb_tile *out, int cap, int *count);
  * generated on the device by the library and only timing is kept): every
  * shape best of 2 whole calls after a warm-up, then the three fastest 5 more
  * times each, interleaved (fused shapes only for n < 2^15). Keep the fastest
- * for n's size class and return it
- * in *best with its rate in interactions per second in *rate (either may be
- * NULL). Synchronous.
+ * for n's size class and return it in *best with its rate in interactions
+ * per second in *rate (either may be NULL). Synchronous.
  */
 nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_tile *best,
                       double *rate);
