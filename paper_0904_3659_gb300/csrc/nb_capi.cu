@@ -210,31 +210,26 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
         e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, plan.partial_bytes);
         if (e == cudaSuccess) e = ensure_counters(ctx, plan.nib);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (partial sums)");
-        PairArgs fa{};
-        fa.partial = static_cast<float4 *>(ctx->d_partial);
-        fa.err = ctx->d_err;
-        fa.njt = plan.njt;
-        fa.units = plan.units;
-        fa.grid = plan.grid;
-        fa.maxseg = plan.maxseg;
-        fa.eps2 = eps * eps;
-        fa.fault_unit = -1;
-        fa.wait_ns = ctx->wait_ns;
-        fa.npad = plan.npad;
-        fa.partial_len = (int64_t)(ctx->partial_bytes / sizeof(float4));
+        FusedArgs fa{};
         fa.x = x;
         fa.m = m;
         fa.n = n;
         fa.a = a;
         fa.p = p;
+        fa.partial = static_cast<float4 *>(ctx->d_partial);
+        fa.partial_len = (int64_t)(ctx->partial_bytes / sizeof(float4));
         fa.counters = ctx->d_count;
+        fa.err = ctx->d_err;
         fa.nib = plan.nib;
+        fa.njt = plan.njt;
         fa.nchunks = plan.nchunks;
+        fa.grid = plan.grid;
+        fa.eps2 = eps * eps;
         fa.a_scale = accel_scale(v.tile.refine);
         fa.p_scale = pot_scale(v.tile.refine);
         {
             TimedLaunch t(ctx, K_PAIR, st);
-            e = v.launch(fa, plan.grid, v.smem, st);
+            e = v.launch_fused(fa, plan.grid, v.smem, st);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "fused pair kernel launch");
         return NB_OK;

@@ -43,16 +43,25 @@ struct PairArgs {
     const float4 *cref;    // per-j-tile reference points (frame variants only)
     int64_t npad;          // entries of jp (bounds checks of the debug build)
     int64_t partial_len;   // float4 entries of partial (debug build)
-    // Fused variants only: they read x, m themselves and the last CTA to
-    // finish an i-block writes its a, p (no pack or combine kernel).
+};
+
+// Arguments of the fused single-launch kernel (small n): it reads x, m
+// itself and the last CTA to finish an i-block writes its a, p.
+struct FusedArgs {
     const float *x;        // [n][3]
     const float *m;        // [n]
     int64_t n;
     float *a;              // [n][3]
     float *p;              // [n]
+    float4 *partial;       // [nib][nchunks][words][ib] per-CTA partial sums
+    int64_t partial_len;   // float4 entries of partial (debug build)
     int *counters;         // [nib] arrivals per i-block; zero between launches
+    int *err;              // device error word (debug build)
     int64_t nib;
+    int64_t njt;           // j-tiles covering n
     int64_t nchunks;       // j-chunks (CTAs) per i-block
+    int grid;              // CTAs launched (nib * nchunks)
+    float eps2;
     float a_scale, p_scale;
 };
 
@@ -99,6 +108,7 @@ struct PairVariant {
     const void *kernel;        // for occupancy queries
     size_t smem;               // dynamic shared memory bytes
     cudaError_t (*launch)(const PairArgs &, int grid, size_t smem, cudaStream_t);
+    cudaError_t (*launch_fused)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
 };
 
 // Registry of compiled variants (nb_pair.cu).

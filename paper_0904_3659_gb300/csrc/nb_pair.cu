@@ -422,7 +422,7 @@ __global__ void reduce_kernel(const ReduceArgs r) {
 constexpr int kFusedJmax = 1024;  // particles per shared-memory block (32 KB)
 
 template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
-__global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const PairArgs args) {
+__global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs args) {
     static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
     static_assert(kFusedJmax % JT == 0, "blocks hold whole tiles");
     constexpr int THREADS = WARPS * 32;
@@ -605,7 +605,7 @@ static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStr
 }
 
 template <int WARPS, int I, int J, int U, int M, bool N, bool C>
-static cudaError_t launch_fused(const PairArgs &a, int grid, size_t smem, cudaStream_t st) {
+static cudaError_t launch_fused(const FusedArgs &a, int grid, size_t smem, cudaStream_t st) {
     fused_kernel<WARPS, I, J, U, M, N, C><<<grid, WARPS * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -622,7 +622,7 @@ constexpr size_t pair_smem() {
 #define NB_VARIANT_F(T, I, J, S, U, M, R, A, X, N, C, F)                                       \
     {{T, I, J, S, U, M, R, A, X, N}, C,                                                         \
      (const void *)pair_kernel<T, I, J, S, U, M, R, A, X, (N != 0), C, F>,                      \
-     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, (N != 0), C, F>}
+     pair_smem<T, I, J, S, A, C>(), launch_pair<T, I, J, S, U, M, R, A, X, (N != 0), C, F>, nullptr}
 #define NB_VARIANT(T, I, J, S, U, M, R, A, X, N, C) NB_VARIANT_F(T, I, J, S, U, M, R, A, X, N, C, false)
 // Fused single-launch shapes: T threads (T / 32 warps sharing one i-block of
 // 32 I particles), J-particle warp tiles, one shared-memory block of
@@ -630,7 +630,7 @@ constexpr size_t pair_smem() {
 #define NB_FUSED(T, I, J, U, M, N, C)                                                        \
     {{T, I, J, 1, U, M, 0, 0, 63, N, 1}, C,                                                     \
      (const void *)fused_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
-     launch_fused<T / 32, I, J, U, M, (N != 0), C>}
+     nullptr, launch_fused<T / 32, I, J, U, M, (N != 0), C>}
 
 // Plain shapes. The first group evaluates the reciprocal square root without
 // the Newton step (refine 0, 13 FP32 ops per pair); the second keeps the
