@@ -41,7 +41,8 @@ WORKLOAD = "plummer1m"
 FLOP_PER_INT_PAPER = 38          # the paper's convention (Section "Experiments")
 FP32_LANES_PER_SM = 128          # FP32 lanes per SM per clock
 MUFU_PER_INT = 1
-# The Newton-step tile of the same shape as the default, timed beside it.
+# The earlier built-in large-N shape, with the Newton step, timed beside the
+# headline (what the step costs).
 NEWTON_TILE = (128, 8, 256, 3, 8, 1, 1, 0, 63, 1, 0)
 
 
