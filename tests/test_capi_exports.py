@@ -56,6 +56,12 @@ def test_host_only_calls(lib):
     # unit's rsqrt as is (the built-in default) and with one Newton step.
     for mode in (lib.NB_PLAIN, lib.NB_COMPENSATED):
         assert {t.refine for t in lib.nb_list_tiles(mode)} == {0, 1}
+    # The adjoint kernel's shapes: packed pairs, tiles dividing the padding.
+    vjp = lib.nb_list_vjp_tiles()
+    assert len(vjp) >= 2
+    for t in vjp:
+        assert t.ipt % 2 == 0 and 3072 % (t.threads * t.ipt) == 0 and 3072 % t.jtile == 0
+        assert t.stages >= 2 and t.threads % 32 == 0 and t.fused == 0
 
 
 def test_tile_struct_matches_header(lib):

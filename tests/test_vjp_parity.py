@@ -118,6 +118,9 @@ def test_every_vjp_shape(nb, ctx, oracle_mod):
     sx, sm = vjp_term_scales(x32, m32, eps, ga, gp)
     tiles = nb.nb_list_vjp_tiles()
     assert len(tiles) >= 2
+    with pytest.raises(nb.NBError) as e:  # not a compiled shape
+        nb.nb_set_vjp_tile(ctx, (96, 2, 100, 3, 2, 1, 0, 0, 63, 0, 0))
+    assert e.value.status == nb.NB_ERR_ARG
     try:
         for t in tiles:
             nb.nb_set_vjp_tile(ctx, t)
