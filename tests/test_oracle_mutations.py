@@ -78,6 +78,45 @@ def test_planted_mistake_is_caught(tmp_path, name):
     assert failed, f"no pin caught the planted mistake {name}"
 
 
+# Planted mistakes in the reverse-mode trajectory gradient (Python, oracle.Oracle.
+# leapfrog_grad): each must make its central-difference pin fail.
+PY_MUTATIONS = {
+    "grad_back_kick_sign": ("ab_next = ab - 0.5 * dt * vb", "ab_next = ab + 0.5 * dt * vb"),
+    "grad_drift_dt2_term": ("ab = -0.5 * dt * vb - 0.5 * dt * dt * xb", "ab = -0.5 * dt * vb"),
+    "grad_drift_half_dt": ("vb = vb + dt * xb", "vb = vb + 0.5 * dt * xb"),
+    "grad_force_at_step_start": ("self.force_vjp(xs[s + 1], m, eps, ab_next, zero_p)",
+                                 "self.force_vjp(xs[s], m, eps, ab_next, zero_p)"),
+    "grad_mass_term_dropped": ("mb = mb + gm\n", "mb = mb\n"),
+    "grad_first_force_dropped": ("return xb + gx, vb, mb + gm", "return xb, vb, mb"),
+}
+
+
+def _mutated_grad_oracle(old, new):
+    import textwrap
+    import types
+    src = textwrap.dedent(inspect.getsource(oracle.Oracle.leapfrog_grad))
+    if old:
+        assert src.count(old) == 1, f"mutation does not match leapfrog_grad exactly once: {old!r}"
+        src = src.replace(old, new)
+    ns = dict(vars(oracle))
+    exec(compile(src, "<mutated leapfrog_grad>", "exec"), ns)
+    inst = oracle.Oracle()
+    inst.leapfrog_grad = types.MethodType(ns["leapfrog_grad"], inst)
+    return inst
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_planted_gradient_mistake_is_caught(name):
+    mut = _mutated_grad_oracle(*PY_MUTATIONS[name])
+    with pytest.raises(AssertionError):
+        dyn.test_leapfrog_grad_matches_central_differences(mut)
+
+
+def test_unmutated_gradient_copy_passes():
+    # The harness itself: the method re-executed unchanged passes its pin.
+    dyn.test_leapfrog_grad_matches_central_differences(_mutated_grad_oracle("", ""))
+
+
 def test_unmutated_copy_passes_every_pin(tmp_path):
     # The harness itself: an unchanged copy built the same way passes.
     lib = oracle.build(force=True, src=SRC, out=str(tmp_path / "libcopy.so"))
