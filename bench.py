@@ -703,6 +703,39 @@ def run_case(args):
         p = torch.empty(n, device=dev)
         fn = lambda: nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p)
         units = float((cl.sizes.astype(np.float64) ** 2).sum())
+    elif case in ("leapfrog", "leapfrog-comp"):
+        w = workloads.WORKLOADS["plummer65536_kdk16"]
+        n = args.n or w["n"]
+        x0, v0, m = workloads.plummer(n, seed=w["seed"])
+        xs = torch.from_numpy(x0).to(dev)
+        vs = torch.from_numpy(v0).to(dev)
+        x, v = xs.clone(), vs.clone()
+        mt = torch.from_numpy(m.astype(np.float32)).to(dev)
+        a = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        mode = nb.NB_PLAIN if case == "leapfrog" else nb.NB_COMPENSATED
+        stream = torch.cuda.Stream(dev)  # graph replay needs a non-default stream
+
+        def fn():
+            x.copy_(xs)
+            v.copy_(vs)
+            nb.nb_leapfrog_step(ctx, x, v, mt, a, None, n, np.float32(w["eps"]), w["dt"], w["steps"],
+                                0, mode, stream)
+
+        def run():
+            with torch.cuda.stream(stream):
+                fn()
+            stream.synchronize()
+        units = float(n) * n * (w["steps"] + 1)
+        for _ in range(args.warmup):
+            run()
+        nb.nb_synchronize(ctx, stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run()
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        print(json.dumps({"case": case, "n": n, "ms": ms, "g_units_s": units / (ms * 1e-3) / 1e9}),
+              flush=True)
+        return
     elif case == "vjp":
         n = args.n or 16384
         if args.tile:
@@ -824,7 +857,8 @@ def main(argv=None):
     ap.add_argument("--sweep-sizes", default="4096,16384,65536,262144,1048576")
     ap.add_argument("--sweep-kind", choices=["pair", "vjp"], default="pair",
                     help="which kernel's compiled shapes --sweep times")
-    ap.add_argument("--case", choices=["pair", "comp", "batched", "vjp"], default="",
+    ap.add_argument("--case", choices=["pair", "comp", "batched", "vjp", "leapfrog", "leapfrog-comp"],
+                    default="",
                     help="time one kernel class at a small size (profiler captures)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the leap-frog, batched and adjoint workloads")
