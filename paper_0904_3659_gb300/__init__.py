@@ -320,7 +320,7 @@ def tune_to_file(ctx, sizes, path, modes=(NB_PLAIN, NB_COMPENSATED)):
 
 def load_tuning(ctx, path) -> int:
     """Restore tuning picks saved by tune_to_file; returns how many applied
-    (entries naming a shape this build does not compile are skipped)."""
+    (entries naming a shape the loaded library does not compile are skipped)."""
     import json
     with open(path) as f:
         data = json.load(f)

@@ -623,9 +623,9 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_til
         cudaEventElapsedTime(ms, e0, e1);
         return NB_OK;
     };
-    // Round 1: every shape, warm-up + best of 2. Round 2: the three fastest
+    // Pass 1: every shape, warm-up + best of 2. Pass 2: the three fastest
     // again, 5 times each, interleaved so that a clock change affects them
-    // alike; each keeps its best time over both rounds.
+    // alike; each keeps its best time over both passes.
     const int nv = pair_variant_count(comp);
     std::vector<float> best_ms_of(nv, 0.f);
     std::vector<int> order;  // the shapes timed
