@@ -133,6 +133,25 @@ def library():
     return _lib
 
 
+def _dev(t, dtype: str, numel: int, name: str) -> Optional[int]:
+    """Address of a device array argument, checked: a torch tensor must have
+    the dtype the C signature takes, be contiguous, hold at least `numel`
+    elements and live on a CUDA device (an int is taken as a raw address,
+    None as NULL). A wrong tensor raises here instead of being read as
+    something else by the kernels."""
+    if t is None or isinstance(t, int):
+        return t
+    if str(t.dtype) != "torch." + dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    return t.data_ptr()
+
+
 def _addr(t) -> Optional[int]:
     """Address of a tensor's data (or an int address / None) for a C pointer."""
     if t is None:
@@ -208,8 +227,10 @@ def nb_status_string(status: int) -> str:
 
 
 def nb_force(ctx, x, m, n, eps, a, p, mode=NB_PLAIN, stream=None):
-    _check(ctx, library().nb_force(ctx.handle, _addr(x), _addr(m), int(n), float(eps),
-                                   _addr(a), _addr(p), int(mode), _stream(stream)))
+    n = int(n)
+    args = (_dev(x, "float32", 3 * n, "x"), _dev(m, "float32", n, "m"), n, float(eps),
+            _dev(a, "float32", 3 * n, "a"), _dev(p, "float32", n, "p"))
+    _check(ctx, library().nb_force(ctx.handle, *args, int(mode), _stream(stream)))
 
 
 def nb_force_host(ctx, x, m, n, eps, a, p, mode=NB_PLAIN, stream=None):
@@ -223,50 +244,68 @@ def nb_reserve(ctx, n, mode=NB_PLAIN):
 
 def nb_force_batched(ctx, x, m, offsets, n_clusters, n_total, eps, a, p, mode=NB_PLAIN,
                      stream=None):
-    _check(ctx, library().nb_force_batched(ctx.handle, _addr(x), _addr(m), _addr(offsets),
-                                           int(n_clusters), int(n_total), _addr(eps), _addr(a),
-                                           _addr(p), int(mode), _stream(stream)))
+    nt, nc = int(n_total), int(n_clusters)
+    args = (_dev(x, "float32", 3 * nt, "x"), _dev(m, "float32", nt, "m"),
+            _dev(offsets, "int64", nc + 1, "offsets"), nc, nt, _dev(eps, "float32", nc, "eps"),
+            _dev(a, "float32", 3 * nt, "a"), _dev(p, "float32", nt, "p"))
+    _check(ctx, library().nb_force_batched(ctx.handle, *args, int(mode), _stream(stream)))
 
 
 def nb_leapfrog_step(ctx, x, v, m, a, p, n, eps, dt, nsteps, a_valid, mode=NB_PLAIN, stream=None):
-    _check(ctx, library().nb_leapfrog_step(ctx.handle, _addr(x), _addr(v), _addr(m), _addr(a),
-                                           _addr(p), int(n), float(eps), float(dt), int(nsteps),
+    n = int(n)
+    args = (_dev(x, "float64", 3 * n, "x"), _dev(v, "float64", 3 * n, "v"),
+            _dev(m, "float32", n, "m"), _dev(a, "float32", 3 * n, "a"), _dev(p, "float32", n, "p"))
+    _check(ctx, library().nb_leapfrog_step(ctx.handle, *args, n, float(eps), float(dt), int(nsteps),
                                            int(a_valid), int(mode), _stream(stream)))
 
 
 def nb_leapfrog_adjoint(ctx, x, v, a, m, n, eps, dt, nsteps, lx, lv, la, lm, apply_first,
                         mode=NB_PLAIN, stream=None):
+    n = int(n)
     _check(ctx, library().nb_leapfrog_adjoint(
-        ctx.handle, _addr(x), _addr(v), _addr(a), _addr(m), int(n), float(eps), float(dt),
-        int(nsteps), _addr(lx), _addr(lv), _addr(la), _addr(lm), int(bool(apply_first)), int(mode),
-        _stream(stream)))
+        ctx.handle, _dev(x, "float64", 3 * n, "x"), _dev(v, "float64", 3 * n, "v"),
+        _dev(a, "float32", 3 * n, "a"), _dev(m, "float32", n, "m"), n, float(eps), float(dt),
+        int(nsteps), _dev(lx, "float64", 3 * n, "lx"), _dev(lv, "float64", 3 * n, "lv"),
+        _dev(la, "float64", 3 * n, "la"), _dev(lm, "float64", n, "lm"), int(bool(apply_first)),
+        int(mode), _stream(stream)))
 
 
 def nb_leapfrog_batched_step(ctx, x, v, m, offsets, n_clusters, n_total, eps, a, p, dt, nsteps,
                              a_valid, mode=NB_PLAIN, stream=None):
+    nt, nc = int(n_total), int(n_clusters)
     _check(ctx, library().nb_leapfrog_batched_step(
-        ctx.handle, _addr(x), _addr(v), _addr(m), _addr(offsets), int(n_clusters), int(n_total),
-        _addr(eps), _addr(a), _addr(p), float(dt), int(nsteps), int(a_valid), int(mode),
+        ctx.handle, _dev(x, "float64", 3 * nt, "x"), _dev(v, "float64", 3 * nt, "v"),
+        _dev(m, "float32", nt, "m"), _dev(offsets, "int64", nc + 1, "offsets"), nc, nt,
+        _dev(eps, "float32", nc, "eps"), _dev(a, "float32", 3 * nt, "a"),
+        _dev(p, "float32", nt, "p"), float(dt), int(nsteps), int(a_valid), int(mode),
         _stream(stream)))
 
 
 def nb_energy(ctx, x, v, m, n, eps, mode=NB_PLAIN, stream=None):
     out = (ctypes.c_double * 2)()
-    _check(ctx, library().nb_energy(ctx.handle, _addr(x), _addr(v), _addr(m), int(n), float(eps),
-                                    ctypes.cast(out, _P), int(mode), _stream(stream)))
+    n = int(n)
+    _check(ctx, library().nb_energy(ctx.handle, _dev(x, "float64", 3 * n, "x"),
+                                    _dev(v, "float64", 3 * n, "v"), _dev(m, "float32", n, "m"), n,
+                                    float(eps), ctypes.cast(out, _P), int(mode), _stream(stream)))
     return float(out[0]), float(out[1])
 
 
 def nb_force_vjp(ctx, x, m, n, eps, ga, gp, gx, gm, stream=None):
-    _check(ctx, library().nb_force_vjp(ctx.handle, _addr(x), _addr(m), int(n), float(eps),
-                                       _addr(ga), _addr(gp), _addr(gx), _addr(gm),
+    n = int(n)
+    _check(ctx, library().nb_force_vjp(ctx.handle, _dev(x, "float32", 3 * n, "x"),
+                                       _dev(m, "float32", n, "m"), n, float(eps),
+                                       _dev(ga, "float32", 3 * n, "ga"), _dev(gp, "float32", n, "gp"),
+                                       _dev(gx, "float32", 3 * n, "gx"), _dev(gm, "float32", n, "gm"),
                                        _stream(stream)))
 
 
 def nb_force_noalloc(x, m, n, eps, a, p, stream=None):
     """Allocation-free nb_force (no context; n <= 65536; waits for the stream)."""
-    _check(None, library().nb_force_noalloc(_addr(x), _addr(m), int(n), float(eps), _addr(a),
-                                            _addr(p), _stream(stream)))
+    n = int(n)
+    _check(None, library().nb_force_noalloc(_dev(x, "float32", 3 * n, "x"),
+                                            _dev(m, "float32", n, "m"), n, float(eps),
+                                            _dev(a, "float32", 3 * n, "a"),
+                                            _dev(p, "float32", n, "p"), _stream(stream)))
 
 
 def nb_synchronize(ctx, stream=None):

@@ -79,3 +79,27 @@ def test_create_reports_error_without_gpu(lib):
     with pytest.raises(lib.NBError) as e:
         lib.Context(0)
     assert e.value.status in (lib.NB_ERR_CUDA, lib.NB_ERR_ARG)
+
+
+def test_binding_validates_device_arguments(lib):
+    # Wrong dtype, layout, size or device is refused by the binding before
+    # any library call (no GPU needed: the checks run first).
+    torch = pytest.importorskip("torch")
+    n = 10
+    x32 = torch.zeros((n, 3), dtype=torch.float32)
+    m32 = torch.zeros(n, dtype=torch.float32)
+    a32, p32 = torch.zeros((n, 3)), torch.zeros(n)
+    with pytest.raises(TypeError, match="x must be float32"):
+        lib.nb_force(None, x32.double(), m32, n, 0.1, a32, p32)
+    with pytest.raises(ValueError, match="contiguous"):
+        lib.nb_force(None, torch.zeros((3, n)).t(), m32, n, 0.1, a32, p32)
+    with pytest.raises(ValueError, match="needs 30"):
+        lib.nb_force(None, x32[:9], m32, n, 0.1, a32, p32)
+    with pytest.raises(TypeError, match="CUDA"):
+        lib.nb_force(None, x32, m32, n, 0.1, a32, p32)
+    with pytest.raises(TypeError, match="x must be float64"):
+        lib.nb_leapfrog_step(None, x32, x32, m32, a32, None, n, 0.1, 0.01, 1, 0)
+    with pytest.raises(TypeError, match="offsets must be int64"):
+        # (raw integer addresses pass unchecked; offsets is checked next)
+        lib.nb_force_batched(None, 0, 0, torch.zeros(2, dtype=torch.int32), 1, n,
+                             torch.zeros(1), a32, p32)
