@@ -33,7 +33,13 @@
  *    NULL pointer where data is needed, or eps not finite or not > 0
  *    (the paper's eps exists to prevent division by zero) is NB_ERR_ARG.
  *    Non-finite positions or masses are not checked; they propagate.
- *  - Contexts are not thread-safe: use one per host thread.
+ *  - Contexts are not thread-safe: use one per host thread. A context's
+ *    scratch (packed particles, partial sums, the fused shapes' per-i-block
+ *    arrival counts) is shared by all its calls, so calls on one context must
+ *    execute in order on the GPU (one stream, or streams ordered by events);
+ *    work that must overlap on the GPU needs one context per stream.
+ *  - Graph capture: once nb_reserve has sized the scratch for the (n, mode)
+ *    used, nb_force allocates nothing and can be captured into a CUDA graph.
  */
 #ifndef NBODY_H
 #define NBODY_H
