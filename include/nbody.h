@@ -10,6 +10,9 @@
  *     p_i = sum_{j != i} m_j / (|x_i - x_j|^2 + eps^2)^{1/2}
  *
  * and, around it, the leap-frog integrator of Section "Method", Eqs. (1)-(3).
+ * Each compute entry point names the passage that defines its operation;
+ * the context, tuning, timing and error entry points are engineering support
+ * with no counterpart in the paper.
  *
  * Conventions shared by every entry point:
  *  - Sign: a and p are returned exactly as printed in Eq. (gravity): a_i
@@ -153,7 +156,7 @@ nb_status nb_force(nb_ctx *ctx, const float *x, const float *m, int64_t n, float
                    float *a, float *p, nb_mode mode, void *stream);
 
 /*
- * nb_force on HOST buffers: copies x and m to the device, runs nb_force,
+ * Eq. (gravity) on HOST buffers: copies x and m to the device, runs nb_force,
  * copies a and p back and waits for the copies to finish. Same argument
  * meaning as nb_force, but all four arrays are host memory (pinned memory
  * gives the fastest copies). Device staging buffers are owned by ctx.
@@ -185,7 +188,8 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
                            float *a, float *p, nb_mode mode, void *stream);
 
 /*
- * nb_leapfrog_step for a batch of independent clusters (as nb_force_batched):
+ * nb_leapfrog_step (Eqs. (1)-(3) of Section "Method") for a batch of
+ * independent clusters, each with its own Eq. (gravity) (as nb_force_batched):
  * x, v FP64 device [n_total][3] in/out; m, eps, offsets as in
  * nb_force_batched; a [n_total][3] FP32 device, in (if a_valid) / out;
  * p [n_total] FP32 device, out. One persistent pair launch per step; steps
@@ -251,8 +255,10 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
                               nb_mode mode, void *stream);
 
 /*
- * Total energy of an FP64 state: out_kw[0] = K = 1/2 sum m |v|^2 and
- * out_kw[1] = W = -1/2 sum m_i p_i, accumulated in FP64 in a fixed order.
+ * Total energy of an FP64 state, the conservation check of a leap-frog run
+ * (the paper computes no energy): out_kw[0] = K = 1/2 sum m |v|^2 and
+ * out_kw[1] = W = -1/2 sum m_i p_i with p from Eq. (gravity), accumulated in
+ * FP64 in a fixed order.
  * x, v FP64 device [n][3]; m FP32 device [n]; out_kw HOST double[2].
  * Synchronous (waits for `stream`).
  */
@@ -330,12 +336,14 @@ nb_status nb_set_tuned_tile(nb_ctx *ctx, int64_t n, nb_mode mode, const nb_tile 
 nb_status nb_list_tiles(nb_mode mode, nb_tile *out, int cap, int *count);
 
 /*
- * Time every compiled tile shape on synthetic data of size n (the inputs are
- * generated on the device by the library and only timing is kept): every
- * shape best of 2 whole calls after a warm-up, then the three fastest 5 more
- * times each, interleaved (fused shapes only for n < 2^15). Keep the fastest
- * for n's size class and return it in *best with its rate in interactions
- * per second in *rate (either may be NULL). Synchronous.
+ * The unroll depth and tile shape the paper leaves to future work (Section
+ * "Conclusion"), chosen by measurement: time every compiled tile shape on
+ * synthetic data of size n (generated on the device by the library; only
+ * the timing is kept). Every shape is timed best of 2 whole calls after a
+ * warm-up, then the three fastest 5 more times each, interleaved (fused
+ * shapes only for n < 2^15). Keep the fastest for n's size class and return
+ * it in *best with its rate in interactions per second in *rate (either may
+ * be NULL). Synchronous.
  */
 nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_tile *best,
                       double *rate);
