@@ -269,8 +269,10 @@ nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *
  * Vector-Jacobian product of Eq. (gravity): for upstream gradients ga [n][3]
  * on a and gp [n] on p, the gradient of L = sum_i ga_i . a_i + gp_i p_i with
  * respect to the positions, gx [n][3], and masses, gm [n]. All FP32 device
- * arrays. Computed as one gather pass over all pairs (no atomics), so the
- * result is reproducible. Asynchronous.
+ * arrays; gp may be NULL (no upstream gradient on p: a kernel without its
+ * terms runs, 26 instead of 29 FP32 operations per pair). Computed as one
+ * gather pass over all pairs (no atomics), so the result is reproducible.
+ * Asynchronous.
  */
 nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, float eps,
                        const float *ga, const float *gp, float *gx, float *gm, void *stream);

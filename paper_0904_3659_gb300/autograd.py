@@ -44,7 +44,7 @@ class NBForce(torch.autograd.Function):
         x, m = ctx.saved_tensors
         n = x.shape[0]
         ga = torch.zeros_like(x) if ga is None else ga.to(torch.float32).contiguous()
-        gp = torch.zeros_like(m) if gp is None else gp.to(torch.float32).contiguous()
+        gp = None if gp is None else gp.to(torch.float32).contiguous()  # None: p unused
         gx = torch.empty_like(x)
         gm = torch.empty_like(m)
         nb_force_vjp(ctx.nbctx, x, m, n, ctx.eps, ga, gp, gx, gm)

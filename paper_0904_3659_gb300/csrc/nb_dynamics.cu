@@ -446,11 +446,12 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
     const size_t n3 = (size_t)3 * n;
 
     // One scratch buffer: replayed x, v (FP64), positions of every step
-    // (FP64), replayed a, p and the VJP kernel's operands and results (FP32).
+    // (FP64), replayed a, p and the VJP kernel's operands and results (FP32;
+    // the trajectory has no upstream gradient on p, so the VJP gets none).
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t b_xv = al(n3 * sizeof(double)), b_hist = al((size_t)(nsteps + 1) * n3 * sizeof(double));
     const size_t b_v3 = al(n3 * sizeof(float)), b_s = al((size_t)n * sizeof(float));
-    const size_t total = 2 * b_xv + b_hist + 4 * b_v3 + 3 * b_s;
+    const size_t total = 2 * b_xv + b_hist + 4 * b_v3 + 2 * b_s;
     if ((st = ensure_slot(ctx, S_ADJ, total)) != NB_OK) return st;
     float *pbuf = nullptr;
     if ((st = reserve_leapfrog(ctx, n, mode, nullptr, &pbuf)) != NB_OK) return st;
@@ -462,8 +463,7 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
     float *x32 = aw + b_v3 / sizeof(float);
     float *ga32 = x32 + b_v3 / sizeof(float);
     float *gx32 = ga32 + b_v3 / sizeof(float);
-    float *gp32 = gx32 + b_v3 / sizeof(float);
-    float *gm32 = gp32 + b_s / sizeof(float);
+    float *gm32 = gx32 + b_v3 / sizeof(float);
     float *pw = gm32 + b_s / sizeof(float);
 
     // Replay the segment on copies with the forward's own kernels (same
@@ -471,7 +471,6 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
     cudaError_t e = cudaMemcpyAsync(xw, x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(vw, v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && a) e = cudaMemcpyAsync(aw, a, n3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(gp32, 0, (size_t)n * sizeof(float), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint replay copies");
     st = mode == NB_COMPENSATED
              ? leapfrog_frames(ctx, xw, vw, m, aw, pw, n, eps, dt, nsteps, a != nullptr, s, hist)
@@ -483,14 +482,16 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
     for (int t = nsteps - 1; t >= 0; --t) {
         adj_back_kick_kernel<<<nb3, 256, 0, s>>>(la, lv, hist + (size_t)(t + 1) * n3, n, dt, ga32, x32);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint kick launch");
-        if ((st = nb_force_vjp(ctx, x32, m, n, eps, ga32, gp32, gx32, gm32, stream)) != NB_OK) return st;
+        if ((st = nb_force_vjp(ctx, x32, m, n, eps, ga32, nullptr, gx32, gm32, stream)) != NB_OK)
+            return st;
         adj_drift_kick_kernel<<<nb3, 256, 0, s>>>(lx, lv, la, lm, gx32, gm32, n, dt);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint drift launch");
     }
     if (apply_first) {
         adj_first_operands_kernel<<<nb3, 256, 0, s>>>(la, hist, n, ga32, x32);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
-        if ((st = nb_force_vjp(ctx, x32, m, n, eps, ga32, gp32, gx32, gm32, stream)) != NB_OK) return st;
+        if ((st = nb_force_vjp(ctx, x32, m, n, eps, ga32, nullptr, gx32, gm32, stream)) != NB_OK)
+            return st;
         adj_first_fold_kernel<<<nb3, 256, 0, s>>>(lx, la, lm, gx32, gm32, n);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }

@@ -24,7 +24,8 @@
 //    h_l = -4 gp_l: y^3 = -u^3/8 and y^5 = -u^5/32 give C = 32 c_il, G = 8 gm_i,
 //    so gx_i = R/32 - ga_i S/8 + m_i V/8, gm_i = G/8; 32 operations.
 // All scale factors are exact powers of two; one special-function
-// reciprocal square root per pair.
+// reciprocal square root per pair. With no upstream gradient on p (gp NULL)
+// the terms in h vanish: C = u^5 a and G = sum (r.ga_l) u^3, 26 operations.
 #include <algorithm>
 #include <cmath>
 
@@ -66,7 +67,7 @@ __global__ void vjp_pack_kernel(const float *__restrict__ x, const float *__rest
         v[4] = ga[3 * i];
         v[5] = ga[3 * i + 1];
         v[6] = ga[3 * i + 2];
-        v[7] = kVGp * gp[i];
+        v[7] = gp ? kVGp * gp[i] : 0.f;
     }
     float4 *dst = reinterpret_cast<float4 *>(vp + i);
 #pragma unroll
@@ -85,7 +86,7 @@ struct VjpArgs {
     int64_t npad, partial_len;  // extents (debug-build bounds checks)
 };
 
-template <int P, int JT, int UNR, bool DIAG>
+template <int P, int JT, int UNR, bool DIAG, bool GP>
 __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const float2 (&xi)[P],
                                          const float2 (&yi)[P], const float2 (&zi)[P],
                                          const float2 (&g3x)[P], const float2 (&g3y)[P],
@@ -121,8 +122,13 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
             const float2 dgi3 = fma2(dz, g3z[q], fma2(dy, g3y[q], mul2(dx, g3x[q])));  // 3 r.ga_i
             const float2 dgj = fma2(dz, gzj, fma2(dy, gyj, mul2(dx, gxj)));           // r.ga_l
             const float2 a3 = fma2(mj, dgi3, mul2(nm3[q], dgj));
-            const float2 b4 = fma2(gp4[q], mj, mul2(nm[q], gp4nj));
-            const float2 c32 = mul2(u3, fma2(u2, a3, b4));  // u^5 a3 + u^3 b4
+            float2 c32;
+            if (GP) {
+                const float2 b4 = fma2(gp4[q], mj, mul2(nm[q], gp4nj));
+                c32 = mul2(u3, fma2(u2, a3, b4));  // u^5 a3 + u^3 b4
+            } else {
+                c32 = mul2(u3, mul2(u2, a3));  // u^5 a3
+            }
             acc[q][0] = fma2(c32, dx, acc[q][0]);
             acc[q][1] = fma2(c32, dy, acc[q][1]);
             acc[q][2] = fma2(c32, dz, acc[q][2]);
@@ -130,7 +136,7 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
             acc[q][4] = fma2(u3, gxj, acc[q][4]);
             acc[q][5] = fma2(u3, gyj, acc[q][5]);
             acc[q][6] = fma2(u3, gzj, acc[q][6]);
-            acc[q][7] = fma2(gp4nj, u, fma2(dgj, u3, acc[q][7]));
+            acc[q][7] = GP ? fma2(gp4nj, u, fma2(dgj, u3, acc[q][7])) : fma2(dgj, u3, acc[q][7]);
         }
     }
 }
@@ -138,7 +144,8 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
 // THREADS, IPT (i per thread, in packed pairs), JT (j-tile), STAGES (TMA
 // stages), UNR (unroll of the j loop), ACCS (running sums in shared memory,
 // one slot per thread, touched once per tile: frees 16 registers per pair).
-template <int THREADS, int IPT, int JT, int STAGES, int UNR, int ACCS>
+// GP: the upstream gradient on p is not zero (its terms are summed).
+template <int THREADS, int IPT, int JT, int STAGES, int UNR, int ACCS, bool GP>
 __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
     constexpr int P = IPT / 2;
     constexpr int IB = THREADS * IPT;
@@ -265,10 +272,11 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
                 self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
                 self1[q] = self0[q] + THREADS;
             }
-            vjp_tile<P, JT, 1, true>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0, self1);
+            vjp_tile<P, JT, 1, true, GP>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
+                                         self1);
         } else {
-            vjp_tile<P, JT, UNR, false>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
-                                     self1);
+            vjp_tile<P, JT, UNR, false, GP>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2,
+                                         self0, self1);
         }
 #pragma unroll
         for (int q = 0; q < P; ++q)
@@ -349,14 +357,14 @@ enum VSlot : int { V_VP = SLOT_VJP_VP, V_PART = SLOT_VJP_PART };
 // sums_in_smem; the others fixed). Entry kVjpDefault is the built-in choice.
 struct VjpVariant {
     nb_tile tile;
-    const void *kernel;
+    const void *kernel[2];  // [0]: no upstream gradient on p; [1]: with it
     size_t smem;
-    void (*launch)(const VjpArgs &, int grid, size_t smem, cudaStream_t);
+    void (*launch[2])(const VjpArgs &, int grid, size_t smem, cudaStream_t);
 };
 
-template <int T, int I, int J, int S, int U, int A>
+template <int T, int I, int J, int S, int U, int A, bool G>
 void launch_vjp(const VjpArgs &a, int grid, size_t smem, cudaStream_t st) {
-    vjp_kernel<T, I, J, S, U, A><<<grid, T, smem, st>>>(a);
+    vjp_kernel<T, I, J, S, U, A, G><<<grid, T, smem, st>>>(a);
 }
 
 template <int T, int I, int J, int S, int A>
@@ -365,9 +373,11 @@ constexpr size_t vjp_smem() {
            (size_t)S * sizeof(uint64_t);
 }
 
-#define NB_VJP(T, I, J, S, U, A)                                                         \
-    {{T, I, J, S, U, 1, 0, A, 63, kDefaultRefine, 0}, (const void *)vjp_kernel<T, I, J, S, U, A>, \
-     vjp_smem<T, I, J, S, A>(), launch_vjp<T, I, J, S, U, A>}
+#define NB_VJP(T, I, J, S, U, A)                                                             \
+    {{T, I, J, S, U, 1, 0, A, 63, kDefaultRefine, 0},                                        \
+     {(const void *)vjp_kernel<T, I, J, S, U, A, false>,                                    \
+      (const void *)vjp_kernel<T, I, J, S, U, A, true>},                                    \
+     vjp_smem<T, I, J, S, A>(), {launch_vjp<T, I, J, S, U, A, false>, launch_vjp<T, I, J, S, U, A, true>}}
 const VjpVariant kVjp[] = {
     NB_VJP(256, 2, 128, 3, 2, 0), NB_VJP(256, 2, 128, 3, 4, 0), NB_VJP(512, 2, 128, 3, 2, 0),
     NB_VJP(128, 2, 128, 3, 2, 0), NB_VJP(256, 2, 256, 3, 2, 0), NB_VJP(64, 4, 128, 3, 2, 0),
@@ -391,15 +401,16 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
     nb_status st = check_common(ctx, n, eps, NB_PLAIN);
     if (st != NB_OK) return st;
     if (n == 0) return NB_OK;
-    if (!x || !m || !ga || !gp || !gx || !gm) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
+    if (!x || !m || !ga || !gx || !gm) return fail(ctx, NB_ERR_ARG, "NULL array pointer");
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     const VjpVariant &vv = vjp_variant(ctx);
+    const int with_gp = gp ? 1 : 0;
     PairVariant shape{};
     shape.tile = vv.tile;
     shape.comp = true;  // two float4 words per i
-    shape.kernel = vv.kernel;
+    shape.kernel = vv.kernel[with_gp];
     shape.smem = vv.smem;
     const PairPlan plan = make_plan(shape, n, resident_ctas(ctx, shape));
 
@@ -431,7 +442,7 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
     A.partial_len = (int64_t)(es.cap[V_PART] / sizeof(float4));
     {
         TimedLaunch t(ctx, 5, s);
-        vv.launch(A, plan.grid, vv.smem, s);
+        vv.launch[with_gp](A, plan.grid, vv.smem, s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp kernel launch");
     vjp_combine_kernel<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(A, plan.ib, gx, gm);

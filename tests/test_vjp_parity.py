@@ -134,6 +134,34 @@ def test_every_vjp_shape(nb, ctx, oracle_mod):
         nb.nb_set_vjp_tile(ctx, None)
 
 
+def test_vjp_without_potential_gradient(nb, ctx, oracle_mod):
+    # gp = NULL (no upstream gradient on p) runs the kernel without the p
+    # terms: it must match the oracle with gp = 0, for every compiled shape.
+    import torch
+    n = 2500
+    x, _, m = workloads.plummer(n, seed=71)
+    x32, m32 = x.astype(np.float32), m.astype(np.float32)
+    ga = np.random.default_rng(72).normal(size=(n, 3)).astype(np.float32)
+    gp0 = np.zeros(n, np.float32)
+    eps = np.float32(1.0 / 64)
+    rgx, rgm = oracle_mod.force_vjp(x32, m32, eps, ga, gp0)
+    sx, sm = vjp_term_scales(x32, m32, eps, ga, gp0)
+    dev = torch.device("cuda:0")
+    xt, mt = torch.from_numpy(x32).to(dev), torch.from_numpy(m32).to(dev)
+    gat = torch.from_numpy(ga).to(dev)
+    try:
+        for t in nb.nb_list_vjp_tiles():
+            nb.nb_set_vjp_tile(ctx, t)
+            gx = torch.full((n, 3), float("nan"), device=dev)
+            gm = torch.full((n,), float("nan"), device=dev)
+            nb.nb_force_vjp(ctx, xt, mt, n, eps, gat, None, gx, gm)
+            nb.nb_synchronize(ctx)
+            assert rel_to_scale(gx.cpu().numpy(), rgx, sx) <= 1e-5, t
+            assert rel_to_scale(gm.cpu().numpy(), rgm, sm) <= 1e-5, t
+    finally:
+        nb.nb_set_vjp_tile(ctx, None)
+
+
 def test_vjp_repeatable_and_dot_product(nb, ctx, oracle_mod):
     # Bit-reproducible; and <J dtheta, w> = <dtheta, J^T w> with J dtheta from
     # a central FP64 difference of the oracle's forward.
