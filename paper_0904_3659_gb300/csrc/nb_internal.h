@@ -117,7 +117,6 @@ struct PairVariant {
 const PairVariant *frames_variant(int64_t n);
 int pair_variant_count(bool comp);
 const PairVariant *pair_variant(bool comp, int idx);
-const PairVariant *pair_variant_find(bool comp, const nb_tile &t);
 int pair_default_index(bool comp, int64_t n);
 // The built-in shape for n among those that read packed particles (not
 // fused), for callers that pack themselves (leap-frog from FP64 state).

@@ -719,10 +719,6 @@ static int pair_variant_index(bool comp, const nb_tile &t) {
     return -1;
 }
 
-const PairVariant *pair_variant_find(bool comp, const nb_tile &t) {
-    return pair_variant(comp, pair_variant_index(comp, t));
-}
-
 // Built-in packed (not fused) choices per size class, from the measured shape
 // sweep (GB300, no Newton step): 2 i per thread and 128-particle tiles while
 // the work cannot fill 152 SMs with large i-blocks, then 4 i per thread in
