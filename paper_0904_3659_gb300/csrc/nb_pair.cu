@@ -1,6 +1,7 @@
 // nb_pair.cu -- the pair kernel of Eq. (gravity) (Fujiwara & Nakasato,
 // arXiv:0904.3659, Section "Introduction") for sm_103a, with its pack and
-// combine kernels.
+// combine kernels, the fused single-launch kernel for small n, the registry
+// of compiled shapes and the work plan.
 //
 // Design (GB300-first; the paper's RV770 unrolled loops, Figs. 1-3, are prior
 // art whose idea -- reuse one loaded x_j for several i -- is kept):
