@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                 self0[q] = ibase + (2 * q) * 32 + lane - jbase;
                 self1[q] = self0[q] + 32;
             }
-            tile_pass<P, JT, 4, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
+            tile_pass<P, JT, 1, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
                                                                     self1);
         } else {
             tile_pass<P, JT, 4, false, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
