@@ -34,7 +34,10 @@
  *    nothing is enqueued, output buffers are untouched, and nb_last_error()
  *    gives a one-line message. n == 0 is a valid no-op. A negative count, a
  *    NULL pointer where data is needed, or eps not finite or not > 0
- *    (the paper's eps exists to prevent division by zero) is NB_ERR_ARG.
+ *    (the paper's eps exists to prevent division by zero) is NB_ERR_ARG, and
+ *    so is an eps whose square is not a normal FP32 number (below about
+ *    1.1e-19 it would flush to zero, above about 1.8e19 overflow); batched
+ *    calls check each cluster's eps on the device (see nb_force_batched).
  *    Non-finite positions or masses are not checked; they propagate.
  *  - Contexts are not thread-safe: use one per host thread. A context's
  *    scratch (packed particles, partial sums, the fused shapes' per-i-block
@@ -176,12 +179,15 @@ nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode);
  *                 offsets[c] .. offsets[c+1]-1; offsets[0] == 0, nondecreasing
  *   eps           [n_clusters] FP32 DEVICE array of per-cluster softening
  *   n_total       offsets[n_clusters] (the total particle count)
- * Asynchronous. Offsets and eps are not read back to the host: the caller
- * guarantees eps > 0 and finite; offsets that do not start at 0, decrease,
- * or do not end at n_total are detected on the device, nothing is read or
- * written, and the next nb_synchronize returns NB_ERR_ARG. Work items are (cluster, block of 128 i-particles),
- * taken from a device queue by one persistent launch, largest clusters first;
- * each item is summed by one CTA in a fixed order (bit-reproducible).
+ * Asynchronous. Offsets and eps are not read back to the host: offsets that
+ * do not start at 0, decrease, or do not end at n_total, and a non-empty
+ * cluster whose eps is not > 0 with eps^2 a finite normal FP32 number, are
+ * detected on the device; then nothing is read or written and the next
+ * nb_synchronize returns NB_ERR_ARG. Work items are (cluster, block of 128 i-particles,
+ * chunk of at most a quarter of its j-range), taken from a device queue by
+ * the warps of one persistent launch, largest clusters first; each item is
+ * summed by one warp in a fixed order and the chunks are added in chunk
+ * order (bit-reproducible).
  */
 nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const int64_t *offsets,
                            int64_t n_clusters, int64_t n_total, const float *eps,

@@ -11,6 +11,7 @@
 // items from an atomic counter. Each item is summed entirely by one CTA in a
 // fixed order, so the results do not depend on which CTA pops what.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 
 #include "nb_device.cuh"
@@ -32,6 +33,7 @@ __host__ __device__ __forceinline__ int64_t chunks_of(int64_t ntiles) {
 
 struct BatchPlanArgs {
     const int64_t *off;   // [C+1] caller's offsets
+    const float *eps;     // [C] caller's softening lengths
     int64_t C;
     int64_t n_total;      // the caller's particle count (offsets[C] must equal it)
     int64_t cap_padded;   // capacity of the padded particle array
@@ -69,10 +71,18 @@ __device__ __forceinline__ int size_class(int64_t psz) {
 __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPlanArgs P) {
     __shared__ int64_t scan[kPlanThreads];
     const int t = threadIdx.x;
-    // Offsets must start at 0, never decrease and end at n_total; otherwise
-    // every cluster is given zero size so no later kernel reads anything.
+    // Offsets must start at 0, never decrease and end at n_total, and every
+    // non-empty cluster's eps must be > 0 with eps^2 a finite normal FP32
+    // number (as for nb_force); otherwise every cluster is given zero size so
+    // no later kernel reads anything.
     int bad = 0;
-    for (int64_t c = t; c < P.C; c += kPlanThreads) bad |= P.off[c + 1] < P.off[c];
+    for (int64_t c = t; c < P.C; c += kPlanThreads) {
+        bad |= P.off[c + 1] < P.off[c];
+        if (P.off[c + 1] > P.off[c]) {
+            const float e = P.eps[c], e2 = e * e;
+            bad |= !(e > 0.f && e2 >= FLT_MIN && e2 <= FLT_MAX);  // also false for NaN
+        }
+    }
     if (t == 0) bad |= (P.off[0] != 0) | (P.off[P.C] != P.n_total);
     const bool valid = !__syncthreads_or(bad);
     if (!valid) {
@@ -576,10 +586,11 @@ nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, Batc
     return NB_OK;
 }
 
-nb_status batch_plan(nb_ctx *ctx, const int64_t *offsets, int64_t C, const BatchPlanHost &h,
-                     cudaStream_t st) {
+nb_status batch_plan(nb_ctx *ctx, const int64_t *offsets, const float *eps, int64_t C,
+                     const BatchPlanHost &h, cudaStream_t st) {
     BatchPlanArgs P{};
     P.off = offsets;
+    P.eps = eps;
     P.C = C;
     P.n_total = h.n_total;
     P.cap_padded = h.cap_padded;
@@ -657,7 +668,7 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchPlanHost h{};
     if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
-    if ((st = batch_plan(ctx, offsets, n_clusters, h, s)) != NB_OK) return st;
+    if ((st = batch_plan(ctx, offsets, eps, n_clusters, h, s)) != NB_OK) return st;
     batch_pack_kernel<float, false><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
         x, m, offsets, static_cast<const int64_t *>(bslot(ctx, B_POFF)),
         static_cast<JPart *>(bslot(ctx, B_JP)));
@@ -682,7 +693,7 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchPlanHost h{};
     if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
-    if ((st = batch_plan(ctx, offsets, n_clusters, h, s)) != NB_OK) return st;
+    if ((st = batch_plan(ctx, offsets, eps, n_clusters, h, s)) != NB_OK) return st;
     const int64_t *poff = static_cast<const int64_t *>(bslot(ctx, B_POFF));
     JPart *jp = static_cast<JPart *>(bslot(ctx, B_JP));
     const unsigned nb3 = (unsigned)((3 * n_total + 255) / 256);

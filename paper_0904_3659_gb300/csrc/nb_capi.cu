@@ -1,6 +1,7 @@
 // nb_capi.cu -- the C ABI declared in include/nbody.h: contexts, argument
 // checks, scratch management, tile selection and tuning, per-kernel timing.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -349,6 +350,9 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
 nb_status check_common(nb_ctx *ctx, int64_t n, float eps, int mode) {
     if (n < 0) return fail(ctx, NB_ERR_ARG, "n must be >= 0");
     if (!std::isfinite(eps) || !(eps > 0.f)) return fail(ctx, NB_ERR_ARG, "eps must be finite and > 0");
+    const float e2 = eps * eps;  // the kernels work with eps^2 in FP32
+    if (!(e2 >= FLT_MIN && e2 <= FLT_MAX))
+        return fail(ctx, NB_ERR_ARG, "eps^2 must be a finite normal FP32 number (about 1.1e-19 <= eps <= 1.8e19)");
     if (mode != NB_PLAIN && mode != NB_COMPENSATED) return fail(ctx, NB_ERR_ARG, "unknown mode");
     return NB_OK;
 }
@@ -524,8 +528,9 @@ nb_status nb_synchronize(nb_ctx *ctx, void *stream) {
                             "; the access was skipped and results are invalid");
         if (word & nbdev::kErrBatchPlan)
             return fail(ctx, NB_ERR_ARG,
-                        "batched offsets are invalid (they must start at 0, never decrease and "
-                        "end at n_total); nothing was computed");
+                        "batched offsets or eps are invalid (offsets must start at 0, never "
+                        "decrease and end at n_total; each non-empty cluster's eps must be > 0 "
+                        "with eps^2 a finite normal FP32 number); nothing was computed");
         return fail(ctx, NB_ERR_CUDA, "device error word set");
     }
     return NB_OK;

@@ -15,6 +15,7 @@
 // (16 MiB). Every GPU on which the library is loaded holds that array until
 // the process exits, whether or not this entry point is ever called.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -60,6 +61,8 @@ extern "C" nb_status nb_force_noalloc(const float *x, const float *m, int64_t n,
     if (n < 0) return noalloc_fail(NB_ERR_ARG, "n must be >= 0");
     if (!std::isfinite(eps) || !(eps > 0.f))
         return noalloc_fail(NB_ERR_ARG, "eps must be finite and > 0");
+    if (!(eps * eps >= FLT_MIN && eps * eps <= FLT_MAX))
+        return noalloc_fail(NB_ERR_ARG, "eps^2 must be a finite normal FP32 number");
     if (n == 0) return NB_OK;
     if (!x || !m || !a || !p) return noalloc_fail(NB_ERR_ARG, "NULL array pointer");
     if (n > kMaxN)

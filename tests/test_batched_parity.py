@@ -113,6 +113,22 @@ def test_invalid_offsets_rejected_without_writes(nb, ctx):
             nb.nb_synchronize(ctx)
         assert e.value.status == nb.NB_ERR_ARG
         assert torch.all(a == 7.0) and torch.all(p == 7.0)
+    # A non-empty cluster whose eps^2 is not a finite normal FP32 number is
+    # rejected the same way; an empty cluster's eps is not read.
+    off = torch.tensor([0, 60, 60, 100], dtype=torch.int64, device=dev)
+    for bad_eps in (0.0, -0.5, float("nan"), float("inf"), 1e-20, 1e20):
+        e3 = torch.tensor([0.1, 0.1, bad_eps], device=dev)
+        a = torch.full((n, 3), 7.0, device=dev)
+        p = torch.full((n,), 7.0, device=dev)
+        nb.nb_force_batched(ctx, x, m, off, 3, n, e3, a, p)
+        with pytest.raises(nb.NBError) as e:
+            nb.nb_synchronize(ctx)
+        assert e.value.status == nb.NB_ERR_ARG, bad_eps
+        assert torch.all(a == 7.0) and torch.all(p == 7.0)
+    e3 = torch.tensor([0.1, float("nan"), 0.1], device=dev)  # the empty cluster's eps
+    nb.nb_force_batched(ctx, x, m, off, 3, n, e3, torch.empty((n, 3), device=dev),
+                        torch.empty(n, device=dev))
+    nb.nb_synchronize(ctx)
 
 
 def test_batched_leapfrog_matches_single_cluster_calls(nb, ctx):

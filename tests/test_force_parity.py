@@ -263,10 +263,15 @@ def test_argument_errors(nb, ctx):
     m = torch.ones(4, device=dev)
     a = torch.empty((4, 3), device=dev)
     p = torch.empty(4, device=dev)
-    for eps in (0.0, -1.0, float("inf"), float("nan")):
+    # eps must be finite and > 0, and eps^2 a normal FP32 number (the kernels
+    # work with eps^2: below ~1.1e-19 it would flush to zero, above ~1.8e19
+    # overflow).
+    for eps in (0.0, -1.0, float("inf"), float("nan"), 1e-20, 1e20):
         with pytest.raises(nb.NBError) as e:
             nb.nb_force(ctx, x, m, 4, eps, a, p)
         assert e.value.status == nb.NB_ERR_ARG
+    for eps in (2e-19, 1e19):  # just inside the range
+        nb.nb_force(ctx, x, m, 4, eps, a, p)
     with pytest.raises(nb.NBError) as e:
         nb.nb_force(ctx, x, m, -1, 0.1, a, p)
     assert e.value.status == nb.NB_ERR_ARG
