@@ -492,7 +492,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs
                     self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
                     self1[q] = self0[q] + 32;
                 }
-                tile_pass<P, JT, 1, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+                // (unrolled like the other tiles: in-process A/B at N = 4096, compensated
+                // 15.4 -> 14.5 us, plain unchanged)
+                tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
             } else {
                 tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
             }
