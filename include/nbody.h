@@ -110,7 +110,11 @@ typedef struct nb_ctx nb_ctx;
  * memory themselves (no pack kernel, no TMA; `stages` = 1); warp w sums the
  * `jtile`-particle tiles w, w + warps, ... and the warps' sums are added in
  * warp order. The last CTA of an i-block to finish adds the chunks' partial
- * sums in chunk order and writes its a, p (no combine kernel). Callers that
+ * sums in chunk order and writes its a, p (no combine kernel). `fused` = 2
+ * is the same kernel with the pair kernel's work split: the (i-block,
+ * `jtile`-particle tile) units are divided into equal contiguous ranges,
+ * one per resident CTA, so a CTA may finish one i-block and start the next;
+ * the last contributing CTA adds the partials in CTA order. Callers that
  * pass packed FP64 state (the leap-frog) use the non-fused shape of the same
  * size class instead. */
 typedef struct nb_tile {
@@ -348,8 +352,8 @@ nb_status nb_list_tiles(nb_mode mode, nb_tile *out, int cap, int *count);
  * "Conclusion"), chosen by measurement: time every compiled tile shape on
  * synthetic data of size n (generated on the device by the library; only
  * the timing is kept). Every shape is timed best of 2 whole calls after a
- * warm-up, then the three fastest 5 more times each, interleaved (fused
- * shapes only for n < 2^15). Keep the fastest for n's size class and return
+ * warm-up, then the three fastest 5 more times each, interleaved
+ * (single-launch shapes only for n < 2^16). Keep the fastest for n's size class and return
  * it in *best with its rate in interactions per second in *rate (either may
  * be NULL). Synchronous.
  */

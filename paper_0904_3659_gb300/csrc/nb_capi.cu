@@ -225,6 +225,8 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
         fa.njt = plan.njt;
         fa.nchunks = plan.nchunks;
         fa.grid = plan.grid;
+        fa.units = plan.units;
+        fa.maxseg = plan.maxseg;
         fa.eps2 = eps * eps;
         fa.a_scale = accel_scale(v.tile.refine);
         fa.p_scale = pot_scale(v.tile.refine);
@@ -635,7 +637,7 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_til
     std::vector<float> best_ms_of(nv, 0.f);
     std::vector<int> order;  // the shapes timed
     for (int k = 0; st == NB_OK && k < nv; ++k) {
-        // Fused shapes are for small n only (one CTA per i-block and chunk).
+        // Single-launch shapes: small n only.
         if (pair_variant(comp, k)->tile.fused && !fused_candidate(n)) continue;
         order.push_back(k);
         ctx->has_override[mi] = true;

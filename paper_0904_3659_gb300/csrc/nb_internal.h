@@ -53,16 +53,19 @@ struct FusedArgs {
     int64_t n;
     float *a;              // [n][3]
     float *p;              // [n]
-    float4 *partial;       // [nib][nchunks][words][ib] per-CTA partial sums
+    float4 *partial;       // per-CTA partial sums: [nib][nchunks][words][ib] (chunked
+                           //   form), [grid][maxseg][words][ib] (stream-K form)
     int64_t partial_len;   // float4 entries of partial (debug build)
     int *counters;         // [nib] arrivals per i-block; zero between launches
     int *err;              // device error word (debug build)
     int64_t nib;
     int64_t njt;           // j-tiles covering n
-    int64_t nchunks;       // j-chunks (CTAs) per i-block
-    int grid;              // CTAs launched (nib * nchunks)
+    int64_t nchunks;       // chunked form: j-chunks (CTAs) per i-block
+    int grid;              // CTAs launched (chunked form: nib * nchunks)
     float eps2;
     float a_scale, p_scale;
+    int64_t units;         // stream-K form: (i-block, j-tile) units, nib * njt
+    int64_t maxseg;        // stream-K form: most i-blocks one CTA's range touches
 };
 
 // Arguments of the deterministic cross-CTA combine.

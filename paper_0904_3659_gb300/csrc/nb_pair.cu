@@ -584,6 +584,183 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stream-K form of the fused kernel (tile field fused = 2), for n up to a few
+// 10^4: the (i-block of IB = 32 IPT, JT-particle tile) units are split over
+// the resident CTAs in equal contiguous ranges, as in pair_kernel, so every
+// SM does the same work; a CTA's range may cover parts of two i-blocks. For
+// each such segment the warps share the segment's tiles as in fused_kernel,
+// the warps' sums are added in warp order, the CTA's partial is written in
+// pair_kernel's layout and the last contributing CTA of the i-block adds the
+// partials in CTA order (the combine kernel's order) and writes a_i, p_i.
+template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
+__global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedArgs args) {
+    static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
+    static_assert(kFusedJmax % JT == 0, "blocks hold whole tiles");
+    constexpr int THREADS = WARPS * 32;
+    constexpr int P = IPT / 2;
+    constexpr int IB = 32 * IPT;
+    constexpr int W = COMP ? 2 : 1;
+    constexpr int TPB = kFusedJmax / JT;
+    static_assert(kPad % IB == 0, "i-blocks must divide the padding");
+    static_assert(WARPS * W * IB * sizeof(float4) <= kFusedJmax * sizeof(JPart),
+                  "the cross-warp sums reuse the particle block");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    JPart *blk = reinterpret_cast<JPart *>(smem);
+    float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after a segment's last block
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = args.n, njt = args.njt;
+    const int64_t c = blockIdx.x;
+    const int64_t u0 = c * args.units / args.grid, u1 = (c + 1) * args.units / args.grid;
+    const int64_t bfirst = u0 / njt;
+    const float2 eps2 = splat2(args.eps2);
+    const float2 zero2 = splat2(0.f);
+
+    for (int64_t b = bfirst; b * njt < u1; ++b) {
+        const int64_t t0 = (u0 > b * njt ? u0 : b * njt) - b * njt;  // this CTA's tiles of b
+        const int64_t t1 = (u1 < (b + 1) * njt ? u1 : (b + 1) * njt) - b * njt;
+        float2 xi[P], yi[P], zi[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int64_t i0 = b * IB + (2 * q) * 32 + lane, i1 = i0 + 32;
+            float3 p0 = make_float3(0.f, 0.f, 0.f), p1 = p0;
+            if (i0 < n) p0 = make_float3(args.x[3 * i0], args.x[3 * i0 + 1], args.x[3 * i0 + 2]);
+            if (i1 < n) p1 = make_float3(args.x[3 * i1], args.x[3 * i1 + 1], args.x[3 * i1 + 2]);
+            xi[q] = make_float2(p0.x, p1.x);
+            yi[q] = make_float2(p0.y, p1.y);
+            zi[q] = make_float2(p0.z, p1.z);
+        }
+        float2 sum[P][4], cmp[P][4];
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sum[q][r] = cmp[q][r] = zero2;
+
+        for (int64_t bt0 = t0; bt0 < t1; bt0 += TPB) {
+            const int64_t bt1 = bt0 + TPB < t1 ? bt0 + TPB : t1;
+            const int cnt = (int)(bt1 - bt0) * JT;
+            for (int k = tid; k < cnt; k += THREADS) {
+                const int64_t j = bt0 * JT + k;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond n: inert (m = 0 at the origin)
+                if (j < n) v = make_float4(args.x[3 * j], args.x[3 * j + 1], args.x[3 * j + 2], args.m[j]);
+                float4 *dst = reinterpret_cast<float4 *>(blk + k);
+                const float hm = -0.5f * v.w;
+                dst[0] = make_float4(-v.x, -v.x, -v.y, -v.y);
+                dst[1] = make_float4(-v.z, -v.z, hm, hm);
+            }
+            __syncthreads();
+            for (int64_t t = bt0 + warp; t < bt1; t += WARPS) {
+                const JPart *T = blk + (t - bt0) * JT;
+                float2 acc[P][4];
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
+                const int64_t ibase = b * IB, jbase = t * JT;
+                int self0[P], self1[P];
+                if (jbase < ibase + IB && ibase < jbase + JT) {
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
+                        self1[q] = self0[q] + 32;
+                    }
+                    tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+                } else {
+                    tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+                }
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        if (COMP) {
+                            // Kahan: true value = sum - cmp.
+                            const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
+                            const float2 tt = add2(sum[q][r], y);
+                            cmp[q][r] = add2(add2(tt, neg2(sum[q][r])), neg2(y));
+                            sum[q][r] = tt;
+                        } else {
+                            sum[q][r] = add2(sum[q][r], acc[q][r]);
+                        }
+                    }
+            }
+            __syncthreads();  // the block is read by every warp before it is refilled or reused
+        }
+
+        // The warps' sums, added in warp order: the CTA's partial for i-block b.
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int i0 = (2 * q) * 32 + lane, i1 = i0 + 32;
+            float4 *dst = red + (int64_t)warp * W * IB;
+            dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
+            dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+            if (COMP) {
+                dst[IB + i0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
+                dst[IB + i1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
+            }
+        }
+        __syncthreads();
+        const int64_t seg = b - bfirst;
+        const int64_t off = (c * args.maxseg + seg) * W * (int64_t)IB;
+        for (int l = tid; l < IB; l += THREADS) {
+            float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int w = 0; w < WARPS; ++w) {
+                const float4 hi = red[(int64_t)w * W * IB + l];
+                const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+                if (COMP) {
+                    const float4 lo = red[(int64_t)w * W * IB + IB + l];
+                    const float lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        float t, e;
+                        two_sum(S[r], h[r], t, e);
+                        S[r] = t;
+                        E[r] = __fadd_rn(E[r], __fsub_rn(e, lw[r]));  // warp value = hi - lo
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) S[r] = __fadd_rn(S[r], h[r]);
+                }
+            }
+            if (NB_IN(args.err, 33, seg < args.maxseg && off + (W - 1) * IB + l < args.partial_len)) {
+                args.partial[off + l] = make_float4(S[0], S[1], S[2], S[3]);
+                if (COMP) args.partial[off + IB + l] = make_float4(-E[0], -E[1], -E[2], -E[3]);
+            }
+        }
+        const int64_t clo = cta_of_unit(b * njt, args.units, args.grid);
+        const int64_t chi = cta_of_unit(b * njt + njt - 1, args.units, args.grid);
+        __threadfence();  // this CTA's partial is visible before it counts itself in
+        __syncthreads();  // (also: every thread is done with red before the next block load)
+        if (tid == 0) {
+            int last = 0;
+            if (NB_IN(args.err, 34, b >= 0 && b < args.nib)) {
+                const int prev = atomicAdd(&args.counters[b], 1);
+                last = prev == (int)(chi - clo);
+                if (last) atomicExch(&args.counters[b], 0);  // every contributor has arrived
+            }
+            s_last = last;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            for (int l = tid; l < IB; l += THREADS) {
+                const int64_t gi = b * IB + l;
+                if (gi >= n) break;
+                float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+                sum_segments<COMP>(args.partial, args.partial_len, args.err, b, l, clo, chi,
+                                   args.units, args.grid, njt, (int)args.maxseg, IB, S, E);
+                args.a[3 * gi + 0] = args.a_scale * __fadd_rn(S[0], E[0]);
+                args.a[3 * gi + 1] = args.a_scale * __fadd_rn(S[1], E[1]);
+                args.a[3 * gi + 2] = args.a_scale * __fadd_rn(S[2], E[2]);
+                args.p[gi] = args.p_scale * __fadd_rn(S[3], E[3]);
+            }
+        }
+        __syncthreads();  // s_last is read by every thread before the next segment writes it
+    }
+}
+
 // Synthetic inputs for tuning runs (timing only; values do not matter
 // beyond being finite): x uniform in [-1, 1)^3 from a 64-bit mixer, m = 1/n.
 __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed) {
@@ -613,6 +790,12 @@ static cudaError_t launch_fused(const FusedArgs &a, int grid, size_t smem, cudaS
     return cudaGetLastError();
 }
 
+template <int WARPS, int I, int J, int U, int M, bool N, bool C>
+static cudaError_t launch_fused_sk(const FusedArgs &a, int grid, size_t smem, cudaStream_t st) {
+    fused_sk_kernel<WARPS, I, J, U, M, N, C><<<grid, WARPS * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int T, int I, int J, int S, int A, bool C>
 constexpr size_t pair_smem() {
     // stages, running sums, their barriers, arrival counters, issue records, abort flag
@@ -634,6 +817,11 @@ constexpr size_t pair_smem() {
     {{T, I, J, 1, U, M, 0, 0, 63, N, 1}, C,                                                     \
      (const void *)fused_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
      nullptr, launch_fused<T / 32, I, J, U, M, (N != 0), C>}
+// The same shapes in stream-K form (fused = 2).
+#define NB_FUSED_SK(T, I, J, U, M, N, C)                                                        \
+    {{T, I, J, 1, U, M, 0, 0, 63, N, 2}, C,                                                        \
+     (const void *)fused_sk_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
+     nullptr, launch_fused_sk<T / 32, I, J, U, M, (N != 0), C>}
 
 // Plain shapes. The first group evaluates the reciprocal square root without
 // the Newton step (refine 0, 13 FP32 ops per pair); the second keeps the
@@ -670,6 +858,7 @@ static const PairVariant kPlain[] = {
     NB_FUSED(256, 4, 32, 4, 1, 0, false),
     NB_FUSED(256, 2, 32, 4, 1, 0, false),
     NB_FUSED(512, 2, 32, 4, 1, 0, false),
+    NB_FUSED_SK(256, 4, 32, 4, 1, 0, false),
 };
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
@@ -694,6 +883,7 @@ static const PairVariant kComp[] = {
     NB_FUSED(256, 4, 32, 4, 1, 0, true),
     NB_FUSED(256, 2, 32, 4, 1, 0, true),
     NB_FUSED(512, 2, 32, 4, 1, 0, true),
+    NB_FUSED_SK(256, 4, 32, 4, 1, 0, true),
 };
 // Frame variants (compensated, per-tile reference points; jtile must be 256,
 // the only tile length the frames pack is compiled for).
@@ -704,6 +894,7 @@ static const PairVariant kFrames[] = {
 #undef NB_VARIANT
 #undef NB_VARIANT_F
 #undef NB_FUSED
+#undef NB_FUSED_SK
 
 const PairVariant *frames_variant(int64_t n) { return n >= (int64_t)1 << 16 ? &kFrames[0] : &kFrames[1]; }
 
@@ -744,25 +935,32 @@ int pair_default_unfused_index(bool comp, int64_t n) {
     return k >= 0 ? k : 0;  // every default above is compiled; 0 guards a stale edit
 }
 
-// Below kFusedMaxN the single-launch shape wins: at N = 4096 a whole call
-// takes 15 us against 31.5 us for pack + pair + combine, at 8192 about the
-// same as the packed shapes, from 16384 on it is slower (GB300).
-constexpr int64_t kFusedMaxN = (int64_t)1 << 14;
+// Single-launch shapes by size (GB300, whole calls, plain / compensated):
+// the chunked form below kChunkedMaxN (N = 4096: 14.4 us against 30.7 us for
+// pack + pair + combine), the stream-K form from there to kFusedMaxN (N =
+// 12288: 76.6 / 80.0 us against 92.2 / 94.4 us for the best packed shapes;
+// N = 16384: 129.0 / 133.5 against 137.2 / 141.3 us), the packed shapes
+// above (N = 24576: stream-K 279.0 / 290.5 us against 280.5 / 280.7).
+constexpr int64_t kChunkedMaxN = (int64_t)1 << 13;
+constexpr int64_t kFusedMaxN = (int64_t)3 << 13;
 
-bool fused_candidate(int64_t n) { return n < 2 * kFusedMaxN; }
+bool fused_candidate(int64_t n) { return n < (int64_t)1 << 16; }
 
 int pair_default_index(bool comp, int64_t n) {
     if (n >= kFusedMaxN) return pair_default_unfused_index(comp, n);
-    static const nb_tile fused{256, 4, 32, 1, 4, 1, 0, 0, 63, kDefaultRefine, 1};
-    static const int idx[2] = {pair_variant_index(false, fused), pair_variant_index(true, fused)};
-    const int k = idx[comp ? 1 : 0];
+    constexpr int R = kDefaultRefine;
+    static const nb_tile chunked{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 1};
+    static const nb_tile streamk{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 2};
+    static const int idx[2][2] = {{pair_variant_index(false, chunked), pair_variant_index(true, chunked)},
+                                  {pair_variant_index(false, streamk), pair_variant_index(true, streamk)}};
+    const int k = idx[n < kChunkedMaxN ? 0 : 1][comp ? 1 : 0];
     return k >= 0 ? k : pair_default_unfused_index(comp, n);
 }
 
 PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
     PairPlan p{};
     p.n = n;
-    if (v.tile.fused) {
+    if (v.tile.fused == 1) {
         // One CTA per (i-block, j-chunk); as many chunks as fill the GPU once.
         p.ib = 32 * v.tile.ipt;
         p.npad = round_up(std::max<int64_t>(n, 1), kPad);
@@ -776,8 +974,11 @@ PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
         p.partial_bytes = (size_t)p.grid * p.words * p.ib * sizeof(float4);
         return p;
     }
+    // Stream-K split of (i-block, j-tile) units over the resident CTAs: the
+    // pair kernel, and the fused kernel's stream-K form (whose warps share
+    // one i-block of 32 ipt particles).
     p.nchunks = 1;
-    p.ib = v.tile.threads * v.tile.ipt;
+    p.ib = (v.tile.fused ? 32 : v.tile.threads) * v.tile.ipt;
     p.npad = round_up(std::max<int64_t>(n, 1), kPad);
     p.nib = (n + p.ib - 1) / p.ib;
     p.njt = (n + v.tile.jtile - 1) / v.tile.jtile;
