@@ -859,6 +859,7 @@ static const PairVariant kPlain[] = {
     NB_FUSED(256, 2, 32, 4, 1, 0, false),
     NB_FUSED(512, 2, 32, 4, 1, 0, false),
     NB_FUSED_SK(256, 4, 32, 4, 1, 0, false),
+    NB_FUSED_SK(128, 4, 32, 4, 1, 0, false),
 };
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
@@ -884,6 +885,7 @@ static const PairVariant kComp[] = {
     NB_FUSED(256, 2, 32, 4, 1, 0, true),
     NB_FUSED(512, 2, 32, 4, 1, 0, true),
     NB_FUSED_SK(256, 4, 32, 4, 1, 0, true),
+    NB_FUSED_SK(128, 4, 32, 4, 1, 0, true),
 };
 // Frame variants (compensated, per-tile reference points; jtile must be 256,
 // the only tile length the frames pack is compiled for).
