@@ -607,6 +607,18 @@ def run_ours(args):
                                "kind": "oracle",
                                "sample": (f"{sample['rows']} random rows x all {n} j of the same "
                                           f"workload, FP64, {sample['seconds']:.1f} s")}
+        # The same oracle on one host core (a short sample of its own).
+        import oracle
+        threads = oracle.num_threads()
+        oracle.set_num_threads(1)
+        try:
+            rate1, sample1, _ = cpu_oracle_rate(x32, m32, eps, target_s=min(3.0, args.cpu_seconds),
+                                                min_rows=8)
+        finally:
+            oracle.set_num_threads(threads)
+        out["cpu_baseline"]["one_core"] = {
+            "value": rate1 / 1e9, "unit": "G-int/s", "cores": 1,
+            "sample": f"{sample1['rows']} random rows x all {n} j, FP64, {sample1['seconds']:.1f} s"}
         out["oracle_error"] = {"rows": int(rows.size),
                                "plain": oracle_errors(a_plain[rows], p_plain[rows], ref),
                                "compensated": oracle_errors(a_comp[rows], p_comp[rows], ref)}
