@@ -116,6 +116,19 @@ def test_default_shapes_skip_newton_step(nb, ctx):
             assert nb.nb_get_tile(ctx, n, mode).refine == 0, (mode, n)
 
 
+def test_default_path_by_size(nb):
+    # Built-in choice without tuning: the chunked single-launch shape below
+    # 8192, its stream-K form up to 24576, pack -> pair -> combine above.
+    fresh = nb.Context(0)
+    try:
+        for mode in (0, 1):
+            for n, fused in ((1, 1), (4096, 1), (8191, 1), (8192, 2), (16384, 2), (24575, 2),
+                             (24576, 0), (1 << 20, 0)):
+                assert nb.nb_get_tile(fresh, n, mode).fused == fused, (mode, n)
+    finally:
+        fresh.close()
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_newton_step_matches_unrefined_accuracy(nb, ctx, oracle_mod, mode):
     # The same shape with and without the Newton step: both within the
