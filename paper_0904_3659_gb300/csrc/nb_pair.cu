@@ -588,8 +588,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs
 // Stream-K form of the fused kernel (tile field fused = 2), for n up to a few
 // 10^4: the (i-block of IB = 32 IPT, JT-particle tile) units are split over
 // the resident CTAs in equal contiguous ranges, as in pair_kernel, so every
-// SM does the same work; a CTA's range may cover parts of two i-blocks. For
-// each such segment the warps share the segment's tiles as in fused_kernel,
+// SM does the same work; a CTA's range may end in the next i-block (or, when
+// there are more i-blocks than CTAs, span several). For each such segment the warps share the segment's tiles as in fused_kernel,
 // the warps' sums are added in warp order, the CTA's partial is written in
 // pair_kernel's layout and the last contributing CTA of the i-block adds the
 // partials in CTA order (the combine kernel's order) and writes a_i, p_i.
