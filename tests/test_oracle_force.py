@@ -140,6 +140,20 @@ def test_permutation_equivariance(oracle_mod):
     np.testing.assert_allclose(p2, p1[perm], rtol=1e-14)
 
 
+def test_rotation_equivariance(oracle_mod):
+    # Eq. (gravity) depends on positions only through x_i - x_j and |x_i - x_j|:
+    # rotating the system rotates every a_i and leaves every p_i unchanged
+    # (FP64 rounding aside). A component taken from the wrong axis fails this.
+    x, m = _rand_system(40, 9)
+    q, r = np.linalg.qr(np.random.default_rng(11).normal(size=(3, 3)))
+    rot = q * np.sign(np.diag(r))  # a random orthogonal matrix
+    a1, p1, amag = oracle_mod.force(x, m, 0.1)
+    a2, p2, _ = oracle_mod.force(x @ rot.T, m, 0.1)
+    err_a = np.linalg.norm(a2 - a1 @ rot.T, axis=1) / amag
+    assert err_a.max() <= 1e-13
+    np.testing.assert_allclose(p2, p1, rtol=1e-13)
+
+
 def test_momentum_invariant(oracle_mod):
     # Pairs are antisymmetric: sum_i m_i a_i = 0 up to FP64 rounding.
     x, v, m = workloads.plummer(300, seed=3)
