@@ -353,6 +353,32 @@ def extra_single_call(nb, ctx, dev, torch):
     return out
 
 
+def extra_mid_call(nb, ctx, dev, torch):
+    """N = 12288 Plummer (seed 0), eps = 0.01: one nb_force call in the range
+    of the stream-K single-launch kernel, launched directly."""
+    n, eps = 12288, np.float32(0.01)
+    x0, _, m = workloads.plummer(n, seed=0)
+    x = torch.from_numpy(x0.astype(np.float32)).to(dev)
+    mt = torch.from_numpy(m.astype(np.float32)).to(dev)
+    a = torch.empty((n, 3), device=dev)
+    p = torch.empty(n, device=dev)
+    out = {"workload": "plummer12288", "n": n}
+    for mode, name in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
+        for _ in range(5):
+            nb.nb_force(ctx, x, mt, n, eps, a, p, mode)
+        reps = 100
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(reps):
+            nb.nb_force(ctx, x, mt, n, eps, a, p, mode)
+        e1.record()
+        nb.nb_synchronize(ctx)
+        us = e0.elapsed_time(e1) / reps * 1e3
+        out[name] = {"us_per_call": us, "gint_s": n * n / (us * 1e-6) / 1e9,
+                     "tile": list(nb.nb_get_tile(ctx, n, mode).as_tuple())}
+    return out
+
+
 def extra_adjoint(nb, ctx, dev, torch, plain_rate):
     """N = 16384 Plummer, eps = 1/64: the VJP pair kernel's rate, and one
     64-step differentiable trajectory (forward + backward, checkpoints every 8)."""
@@ -592,6 +618,7 @@ def run_ours(args):
     if args.extras:
         plain_rate = value / world / 1e9
         for key, fn in (("single_call", lambda: extra_single_call(nb, ctx, dev, torch)),
+                        ("mid_call", lambda: extra_mid_call(nb, ctx, dev, torch)),
                         ("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch)),
                         ("batched", lambda: extra_batched(nb, ctx, dev, torch, plain_rate)),
                         ("adjoint", lambda: extra_adjoint(nb, ctx, dev, torch, plain_rate))):
