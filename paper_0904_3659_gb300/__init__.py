@@ -300,8 +300,15 @@ def nb_force_vjp(ctx, x, m, n, eps, ga, gp, gx, gm, stream=None):
 
 
 def nb_force_noalloc(x, m, n, eps, a, p, stream=None):
-    """Allocation-free nb_force (no context; n <= 65536; waits for the stream)."""
+    """Allocation-free nb_force (no context; n <= 65536; waits for the stream).
+    The arrays must live on the current CUDA device."""
     n = int(n)
+    for name, t in (("x", x), ("m", m), ("a", a), ("p", p)):
+        if getattr(t, "is_cuda", False):
+            import torch
+            if t.device.index != torch.cuda.current_device():
+                raise ValueError(f"{name} is on {t.device}, not on the current device "
+                                 f"cuda:{torch.cuda.current_device()}")
     _check(None, library().nb_force_noalloc(_dev(x, "float32", 3 * n, "x"),
                                             _dev(m, "float32", n, "m"), n, float(eps),
                                             _dev(a, "float32", 3 * n, "a"),

@@ -38,7 +38,9 @@ static __device__ int g_noalloc_err;
 // Per-device set-up, done on the first call on each device. In host code the
 // names g_scratch / g_noalloc_err denote host-side shadows, not device
 // addresses, so the device addresses are looked up with
-// cudaGetSymbolAddress while that device is current.
+// cudaGetSymbolAddress while that device is current. They are kept for the
+// life of the process: a cudaDeviceReset (which unloads the library's device
+// image) leaves them stale, so this entry point is not used after one.
 struct DeviceSetup {
     bool ready = false;
     unsigned char *scratch = nullptr;
@@ -74,6 +76,26 @@ extern "C" nb_status nb_force_noalloc(const float *x, const float *m, int64_t n,
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(NB_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(NB_ERR_ARG, "device index out of range");
+
+    // Every array must live on the current device, where the scratch array
+    // and the kernels are taken from (a pointer of another device would be
+    // read through peer access, or fault).
+    const void *arrays[4] = {x, m, a, p};
+    const char *names[4] = {"x", "m", "a", "p"};
+    for (int k = 0; k < 4; ++k) {
+        cudaPointerAttributes at{};
+        e = cudaPointerGetAttributes(&at, arrays[k]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return noalloc_fail(NB_ERR_ARG, std::string(names[k]) + " is not a CUDA pointer");
+        }
+        const bool ok = at.type == cudaMemoryTypeManaged ||
+                        (at.type == cudaMemoryTypeDevice && at.device == dev);
+        if (!ok)
+            return noalloc_fail(NB_ERR_ARG, std::string(names[k]) +
+                                                " is not device memory of the current device " +
+                                                std::to_string(dev));
+    }
 
     const PairVariant &v = *pair_variant(false, 0);
     DeviceSetup ds;
@@ -154,10 +176,11 @@ extern "C" nb_status nb_force_noalloc(const float *x, const float *m, int64_t n,
     e = launch_reduce(ra, false, st);
     if (e != cudaSuccess) return noalloc_fail(NB_ERR_CUDA, cudaGetErrorString(e));
 
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return noalloc_fail(NB_ERR_CUDA, cudaGetErrorString(e));
+    // The error word is read on the caller's stream, so the call waits for
+    // that stream alone (not for other streams of the device).
     int word = 0;
-    e = cudaMemcpy(&word, ds.err, sizeof(int), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(&word, ds.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return noalloc_fail(NB_ERR_CUDA, cudaGetErrorString(e));
     if (word & nbdev::kErrTimeout)
         return noalloc_fail(NB_ERR_TIMEOUT, "a bounded wait for a shared-memory tile ran out");
