@@ -57,9 +57,9 @@ def alu_peak(sm_count, sm_mhz, ops) -> float:
     return sm_count * sm_mhz * 1e6 * FP32_LANES_PER_SM / ops / 1e9
 
 
-# DRAM bytes (read + write) of one launch of the plain pair kernel, from the
-# ncu capture summarised in profiles/pair_kernel_plain_plummer131072.md
-# (4.257 MB read, 0 written at N = 131072). The kernel reads each j-tile from
+# DRAM bytes (read + write) of one launch of the plain pair kernel, from an
+# ncu capture of that kernel alone on a Plummer sphere of N = 131072
+# (4.257 MB read, 0 written). The kernel reads each j-tile from
 # L2 after its first touch, so DRAM traffic grows with N, not N^2; the bench
 # reports it scaled to its N, and null for any other tile shape.
 PROFILED_TILE = (128, 12, 256, 3, 4, 1, 0, 1, 63, 0, 0)
@@ -227,14 +227,16 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def extra_leapfrog(nb, ctx, dev, torch):
+def extra_leapfrog(nb, ctx, dev, torch, oracle_ref=False):
     """N = 65536 Plummer, eps = 1/128: 16 KDK steps of dt = 1/256 (graph
-    replayed), plain and compensated; energy drift and momentum."""
+    replayed), plain and compensated; energy drift and momentum. With
+    oracle_ref the final states are kept (under "_state") for
+    leapfrog_oracle_error."""
     w = workloads.WORKLOADS["plummer65536_kdk16"]
     x0, v0, m = workloads.plummer(w["n"], seed=w["seed"])
     n, eps, dt, steps = w["n"], np.float32(w["eps"]), w["dt"], w["steps"]
     stream = torch.cuda.Stream(dev)
-    out = {"workload": "plummer65536_kdk16", "n": n, "steps": steps}
+    out = {"workload": "plummer65536_kdk16", "n": n, "steps": steps, "_state": {}}
     for mode, name in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
         x = torch.from_numpy(x0.copy()).to(dev)
         v = torch.from_numpy(v0.copy()).to(dev)
@@ -247,7 +249,8 @@ def extra_leapfrog(nb, ctx, dev, torch):
         nb.nb_leapfrog_step(ctx, x, v, mt, a, p, n, eps, dt, 0, 0, mode, stream)  # a(t0)
         e0, e1 = _events(torch)
         e0.record(stream)
-        nb.nb_leapfrog_step(ctx, x, v, mt, a, p, n, eps, dt, steps, 1, mode, stream)
+        # The integrator needs only a: without p the kernels leave the potential out.
+        nb.nb_leapfrog_step(ctx, x, v, mt, a, None, n, eps, dt, steps, 1, mode, stream)
         e1.record(stream)
         nb.nb_synchronize(ctx, stream)
         ms = e0.elapsed_time(e1)
@@ -258,12 +261,43 @@ def extra_leapfrog(nb, ctx, dev, torch):
                      "rel_energy_drift": abs(E1 - E0) / abs(E0),
                      "momentum_change": float(np.abs(P1 - P0).max()),
                      "momentum_scale": float((m[:, None] * np.abs(v1)).sum())}
+        if oracle_ref:
+            out["_state"][name] = (x.cpu().numpy(), v1, a.cpu().numpy())
     return out
 
 
-def extra_batched(nb, ctx, dev, torch, plain_rate):
+def leapfrog_oracle_error(lf):
+    """The leap-frog block's results against the FP64 oracle's own 16 steps
+    from the same initial state (Eqs. (1)-(3) with Eq. (gravity)): position
+    and velocity differences after the last step, and the returned force
+    against the oracle's at the GPU's final positions, every particle (e_a
+    relative to A_i)."""
+    import oracle
+    w = workloads.WORKLOADS["plummer65536_kdk16"]
+    x0, v0, m = workloads.plummer(w["n"], seed=w["seed"])
+    m = m.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    xr, vr, _ = oracle.leapfrog(x0, v0, m, w["eps"], w["dt"], w["steps"])
+    secs = time.perf_counter() - t0
+    v_scale = float(np.sqrt((vr ** 2).sum(1).mean()))
+    for name, (x, v, a) in lf.pop("_state").items():
+        dx = np.linalg.norm(x - xr, axis=1)
+        dv = np.linalg.norm(v - vr, axis=1)
+        ra, _, ramag = oracle.force(x, m, w["eps"])
+        ea = np.linalg.norm(a.astype(np.float64) - ra, axis=1) / ramag
+        lf[name]["oracle_error"] = {
+            "max_abs_dx": float(dx.max()), "max_abs_dv": float(dv.max()),
+            "max_dv_over_v_rms": float(dv.max() / v_scale),
+            "final_force_max_rel_a": float(ea.max()), "final_force_median_rel_a": float(np.median(ea)),
+            "reference": f"oracle.leapfrog, FP64, {w['steps']} steps, {secs:.1f} s; "
+                         "force: oracle.force at the GPU's final positions, every particle"}
+
+
+def extra_batched(nb, ctx, dev, torch, plain_rate, oracle_ref=False):
     """1024 clusters (N log-uniform in [32, 4096]): one nb_force_batched
-    launch, and 32 graph-replayed batched KDK steps."""
+    launch (plain and compensated), and 32 graph-replayed batched KDK steps
+    in each mode. With oracle_ref the results are kept (under "_state") for
+    batched_oracle_error."""
     w = workloads.WORKLOADS["clusters1024_kdk32"]
     cl = workloads.clusters(w["n_clusters"], seed=w["seed"], nmin=w["nmin"], nmax=w["nmax"])
     n, C = cl.x.shape[0], len(cl.sizes)
@@ -276,35 +310,76 @@ def extra_batched(nb, ctx, dev, torch, plain_rate):
     p = torch.empty(n, device=dev)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
-    for _ in range(3):
-        nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p, nb.NB_PLAIN, stream)
-    reps = 10
-    e0, e1 = _events(torch)
-    e0.record(stream)
-    for _ in range(reps):
-        nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p, nb.NB_PLAIN, stream)
-    e1.record(stream)
-    nb.nb_synchronize(ctx, stream)
-    ms = e0.elapsed_time(e1) / reps
-    rate = pairs / (ms * 1e-3) / 1e9
-    x64 = torch.from_numpy(cl.x.copy()).to(dev)
-    v64 = torch.from_numpy(cl.v.copy()).to(dev)
-    torch.cuda.synchronize(dev)
-    steps = w["steps"]
-    nb.nb_leapfrog_batched_step(ctx, x64, v64, mt, off, C, n, eps, a, p, w["dt"], 0, 0,
-                                nb.NB_PLAIN, stream)
-    e0, e1 = _events(torch)
-    e0.record(stream)
-    nb.nb_leapfrog_batched_step(ctx, x64, v64, mt, off, C, n, eps, a, p, w["dt"], steps, 1,
-                                nb.NB_PLAIN, stream)
-    e1.record(stream)
-    nb.nb_synchronize(ctx, stream)
-    ms_lf = e0.elapsed_time(e1)
-    return {"workload": "clusters1024_kdk32", "clusters": C, "particles": n,
-            "interactions_per_eval": pairs, "ms_per_eval": ms, "gint_s": rate,
-            "fraction_of_plain_rate": rate / plain_rate,
-            "kdk32_ms_per_step": ms_lf / steps,
-            "kdk32_gint_s": pairs * steps / (ms_lf * 1e-3) / 1e9}
+    out = {"workload": "clusters1024_kdk32", "clusters": C, "particles": n,
+           "interactions_per_eval": pairs, "_state": {}}
+    for mode, name in ((nb.NB_PLAIN, "plain"), (nb.NB_COMPENSATED, "compensated")):
+        for _ in range(3):
+            nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p, mode, stream)
+        reps = 10
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        for _ in range(reps):
+            nb.nb_force_batched(ctx, x, mt, off, C, n, eps, a, p, mode, stream)
+        e1.record(stream)
+        nb.nb_synchronize(ctx, stream)
+        ms = e0.elapsed_time(e1) / reps
+        rate = pairs / (ms * 1e-3) / 1e9
+        eval_state = (a.cpu().numpy(), p.cpu().numpy())
+        x64 = torch.from_numpy(cl.x.copy()).to(dev)
+        v64 = torch.from_numpy(cl.v.copy()).to(dev)
+        torch.cuda.synchronize(dev)
+        steps = w["steps"]
+        nb.nb_leapfrog_batched_step(ctx, x64, v64, mt, off, C, n, eps, a, p, w["dt"], 0, 0,
+                                    mode, stream)
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        nb.nb_leapfrog_batched_step(ctx, x64, v64, mt, off, C, n, eps, a, p, w["dt"], steps, 1,
+                                    mode, stream)
+        e1.record(stream)
+        nb.nb_synchronize(ctx, stream)
+        ms_lf = e0.elapsed_time(e1)
+        out[name] = {"ms_per_eval": ms, "gint_s": rate,
+                     "fraction_of_plain_rate": rate / plain_rate,
+                     "kdk32_ms_per_step": ms_lf / steps,
+                     "kdk32_gint_s": pairs * steps / (ms_lf * 1e-3) / 1e9}
+        if oracle_ref:
+            out["_state"][name] = (eval_state, (x64.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy()))
+    out["compensated"]["slowdown_vs_plain"] = out["compensated"]["ms_per_eval"] / out["plain"]["ms_per_eval"]
+    out["compensated"]["kdk32_slowdown_vs_plain"] = (out["compensated"]["kdk32_ms_per_step"]
+                                                     / out["plain"]["kdk32_ms_per_step"])
+    return out
+
+
+def _cluster_errors(xs, m, offsets, eps, a, p):
+    """Max over every particle of every cluster of e_a (relative to A_i) and
+    e_p against oracle.force on that cluster alone."""
+    import oracle
+    wa = wp = 0.0
+    for c in range(len(offsets) - 1):
+        lo, hi = int(offsets[c]), int(offsets[c + 1])
+        if hi == lo:
+            continue
+        ra, rp, ramag = oracle.force(xs[lo:hi], m[lo:hi], eps[c])
+        wa = max(wa, float((np.linalg.norm(a[lo:hi].astype(np.float64) - ra, axis=1) / ramag).max()))
+        wp = max(wp, float((np.abs(p[lo:hi].astype(np.float64) - rp) / rp).max()))
+    return {"max_rel_a": wa, "max_rel_p": wp}
+
+
+def batched_oracle_error(bt):
+    """The batched block's results against the FP64 oracle, every particle of
+    every cluster: the single evaluation on the FP32 inputs, and the force the
+    32-step KDK returns at its final FP64 positions (the oracle evaluated at
+    those same positions)."""
+    w = workloads.WORKLOADS["clusters1024_kdk32"]
+    cl = workloads.clusters(w["n_clusters"], seed=w["seed"], nmin=w["nmin"], nmax=w["nmax"])
+    x32, m32 = cl.x.astype(np.float32), cl.m.astype(np.float32)
+    eps32 = cl.eps.astype(np.float32)
+    t0 = time.perf_counter()
+    for name, ((ea, ep), (xk, ak, pk)) in bt.pop("_state").items():
+        bt[name]["oracle_error"] = {
+            "eval": _cluster_errors(x32, m32, cl.offsets, eps32, ea, ep),
+            "kdk32_final_force": _cluster_errors(xk, m32, cl.offsets, eps32, ak, pk)}
+    bt["oracle_seconds"] = time.perf_counter() - t0
 
 
 def extra_single_call(nb, ctx, dev, torch):
@@ -379,7 +454,7 @@ def extra_mid_call(nb, ctx, dev, torch):
     return out
 
 
-def extra_adjoint(nb, ctx, dev, torch, plain_rate):
+def extra_adjoint(nb, ctx, dev, torch, plain_rate, oracle_ref=False):
     """N = 16384 Plummer, eps = 1/64: the VJP pair kernel's rate, and one
     64-step differentiable trajectory (forward + backward, checkpoints every 8)."""
     from paper_0904_3659_gb300.autograd import leapfrog
@@ -427,11 +502,103 @@ def extra_adjoint(nb, ctx, dev, torch, plain_rate):
         torch.cuda.synchronize(dev)
         times.append(time.perf_counter() - t0)
     traj_s = times[-1]
-    return {"workload": "plummer16384_adjoint64", "n": n,
-            "vjp_ms": vjp_ms, "vjp_gpair_s": n * n / (vjp_ms * 1e-3) / 1e9,
-            "forward_ms_same_n": fwd_ms,
-            "vjp_fraction_of_plain_rate": (n * n / (vjp_ms * 1e-3) / 1e9) / plain_rate,
-            "trajectory_grad_s": traj_s, "trajectory_grad_first_s": times[0]}
+    out = {"workload": "plummer16384_adjoint64", "n": n,
+           "vjp_ms": vjp_ms, "vjp_gpair_s": n * n / (vjp_ms * 1e-3) / 1e9,
+           "forward_ms_same_n": fwd_ms,
+           "vjp_fraction_of_plain_rate": (n * n / (vjp_ms * 1e-3) / 1e9) / plain_rate,
+           "trajectory_grad_s": traj_s, "trajectory_grad_first_s": times[0]}
+    if oracle_ref:
+        out["_state"] = {"vjp": (gx.cpu().numpy(), gm.cpu().numpy(), ga.cpu().numpy(),
+                                 gp.cpu().numpy()),
+                         "grads": {"x": xt.grad.cpu().numpy(), "v": vt.grad.cpu().numpy(),
+                                   "m": mg.grad.cpu().numpy().astype(np.float64)}}
+    return out
+
+
+ADJOINT_FD = os.path.join(ROOT, "tests", "golden", "adjoint_fd_plummer16384.txt")
+
+
+def read_adjoint_fd(path=ADJOINT_FD):
+    """The stored FP64 finite differences of the differentiation workload
+    (written by tests/golden/make_adjoint_fd.py from the oracle):
+    [(kind, i, c, h, fd, adjoint)]."""
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, i, c, h, fd, g = line.split()
+            rows.append((k, int(i), int(c), float(h), float(fd), float(g)))
+    return rows
+
+
+def vjp_term_scales_rows(x, m, eps, ga, gp, rows):
+    """For the listed particles k, the sums over l != k of the magnitudes of
+    the terms of gx_k and gm_k (the VJP's analogue of A_i: the sums cancel
+    strongly, so |g_ref| itself is no scale)."""
+    x = np.asarray(x, np.float64)
+    m = np.asarray(m, np.float64)
+    ga = np.asarray(ga, np.float64)
+    gp = np.asarray(gp, np.float64)
+    e2 = float(np.float32(eps)) ** 2
+    nga = np.linalg.norm(ga, axis=1)
+    sx, sm = np.zeros(rows.size), np.zeros(rows.size)
+    for t, k in enumerate(rows):
+        r = x[k] - x
+        r2 = (r * r).sum(1)
+        y = 1.0 / np.sqrt(r2 + e2)
+        y[k] = 0.0
+        y3, y5, rn = y ** 3, y ** 5, np.sqrt(r2)
+        rgk = np.abs(r @ ga[k])
+        rgl = np.abs((r * ga).sum(1))
+        sx[t] = (m * (y3 * nga[k] + 3 * y5 * rgk * rn + abs(gp[k]) * y3 * rn)).sum() + \
+            m[k] * (y3 * nga + 3 * y5 * rgl * rn + np.abs(gp) * y3 * rn).sum()
+        sm[t] = (rgl * y3 + np.abs(gp) * y).sum()
+    return sx, sm
+
+
+def adjoint_oracle_error(adj):
+    """The adjoint block against the FP64 oracle: the VJP kernel on 512
+    sampled rows (error relative to the sum of term magnitudes), and the
+    trajectory gradient on the 32 stored finite-difference coordinates and,
+    for every coordinate, against the oracle's reverse-mode gradient."""
+    import oracle
+    w = workloads.WORKLOADS["plummer16384_adjoint64"]
+    n, eps = w["n"], np.float32(w["eps"])
+    st = adj.pop("_state")
+    t0 = time.perf_counter()
+    x0, v0, m = workloads.plummer(n, seed=w["seed"])
+    x32, m32 = x0.astype(np.float32), m.astype(np.float32)
+    gx, gm, ga, gp = st["vjp"]
+    rows = workloads.sample_rows(n, 512, seed=6)
+    rgx, rgm = oracle.force_vjp(x32, m32, eps, ga, gp, rows=rows)
+    sx, sm = vjp_term_scales_rows(x32, m32, eps, ga, gp, rows)
+    vjp_err = {"rows": int(rows.size),
+               "max_rel_gx": float((np.linalg.norm(gx[rows] - rgx, axis=1) / sx).max()),
+               "max_rel_gm": float((np.abs(gm[rows] - rgm) / sm).max())}
+    g = st["grads"]
+    fd_rows = read_adjoint_fd()
+    rel = []
+    for kind, i, c, h, fd, _ in fd_rows:
+        v = float(g[kind][i] if kind == "m" else g[kind][i, c])
+        rel.append(abs(v - fd) / abs(fd))
+    m64 = m32.astype(np.float64)
+    y = workloads.targets(x0, seed=w["target_seed"])
+    xT, _, _ = oracle.leapfrog(x0, v0, m64, eps, w["dt"], w["steps"])
+    ref = dict(zip("xvm", oracle.leapfrog_grad(x0, v0, m64, eps, w["dt"], w["steps"], 2 * (xT - y))))
+    every = {}
+    for kind in "xvm":
+        r = ref[kind]
+        e = np.abs(g[kind] - r) / np.maximum(np.abs(r), 1e-3 * np.abs(r).max())
+        every[kind] = {"max": float(e.max()), "p99_9": float(np.percentile(e, 99.9))}
+    adj["oracle_error"] = {
+        "vjp": vjp_err,
+        "trajectory_fd": {"coords": len(rel), "max_rel": float(max(rel)),
+                          "median_rel": float(np.median(rel)),
+                          "reference": "tests/golden/adjoint_fd_plummer16384.txt (FP64 central "
+                                       "differences of the oracle's trajectory)"},
+        "trajectory_every_coordinate": every,
+        "seconds": time.perf_counter() - t0}
 
 
 # --------------------------------------------------------------------------
@@ -617,11 +784,12 @@ def run_ours(args):
                               "speedup_without_step": n_ms / ms_plain}
     if args.extras:
         plain_rate = value / world / 1e9
+        ref = not args.no_cpu_baseline
         for key, fn in (("single_call", lambda: extra_single_call(nb, ctx, dev, torch)),
                         ("mid_call", lambda: extra_mid_call(nb, ctx, dev, torch)),
-                        ("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch)),
-                        ("batched", lambda: extra_batched(nb, ctx, dev, torch, plain_rate)),
-                        ("adjoint", lambda: extra_adjoint(nb, ctx, dev, torch, plain_rate))):
+                        ("leapfrog", lambda: extra_leapfrog(nb, ctx, dev, torch, ref)),
+                        ("batched", lambda: extra_batched(nb, ctx, dev, torch, plain_rate, ref)),
+                        ("adjoint", lambda: extra_adjoint(nb, ctx, dev, torch, plain_rate, ref))):
             try:
                 out[key] = fn()
             except Exception as e:  # reported in the line, the headline stands
@@ -657,7 +825,18 @@ def run_ours(args):
             ref4 = oracle.force(single["x"], single["m"], single["eps"])
             for name in ("plain", "compensated"):
                 out["single_call"][name]["oracle_error_all_rows"] = oracle_errors(*single[name], ref4)
+        # The FP64 oracle's error for the other workloads' results.
+        for key, fn in (("leapfrog", leapfrog_oracle_error), ("batched", batched_oracle_error),
+                        ("adjoint", adjoint_oracle_error)):
+            blk = out.get(key, {})
+            if "_state" in blk:
+                try:
+                    fn(blk)
+                except Exception as e:  # reported in the line, the headline stands
+                    blk["oracle_error"] = {"error": f"{type(e).__name__}: {e}"}
     out.get("single_call", {}).pop("_results", None)
+    for key in ("leapfrog", "batched", "adjoint"):
+        out.get(key, {}).pop("_state", None)
     print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

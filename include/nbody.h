@@ -204,9 +204,13 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
  * nb_force_batched; a [n_total][3] FP32 device, in (if a_valid) / out;
  * p [n_total] FP32 device, out. One persistent pair launch per step; steps
  * after the first are replayed from a CUDA graph when `stream` is not the
- * legacy default stream. In NB_COMPENSATED mode each cluster's FP64
- * positions enter the pair kernel as FP32 offsets from the cluster's
- * centroid (formed in FP64). Asynchronous.
+ * legacy default stream. In NB_COMPENSATED mode the FP64 positions enter
+ * the pair kernel as FP32 offsets from per-tile reference points: each
+ * cluster is ordered along the Morton curve of its bounding box (once per
+ * call, from the entry positions), every 128 consecutive ordered particles
+ * form a tile whose reference point is their FP64 centroid rounded to FP32,
+ * and the offsets are formed in FP64, so x_i - x_j loses about 2^-24 times
+ * a tile's extent rather than 2^-24 |x|. Asynchronous.
  */
 nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const float *m,
                                    const int64_t *offsets, int64_t n_clusters, int64_t n_total,
@@ -224,7 +228,9 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
  *   a    [n][3] FP32 device: on entry Eq. (gravity) at the entry positions
  *                (literal sign) if a_valid != 0, else it is computed first;
  *                on exit Eq. (gravity) at the exit positions
- *   p    [n]    FP32 device, out: potentials at the exit positions (may be NULL)
+ *   p    [n]    FP32 device, out: potentials at the exit positions, or NULL:
+ *                the integrator needs only a, so the force kernels then leave
+ *                the potential out (12 instead of 13 FP32 operations per pair)
  * Asynchronous. In NB_COMPENSATED mode the FP64 positions enter the pair
  * kernel as FP32 offsets from per-tile reference points.
  */
@@ -310,15 +316,18 @@ nb_status nb_list_vjp_tiles(nb_tile *out, int cap, int *count);
  * library holds until the process exits.
  *
  *   x, m, a, p, eps  as in nb_force (FP32 DEVICE arrays of the current
- *                    device; plain arithmetic, NB_PLAIN results)
+ *                    device, else NB_ERR_ARG; plain arithmetic, NB_PLAIN
+ *                    results)
  *   n                at most 65536; larger n, or a device whose work split
  *                    would not fit the array, is rejected with NB_ERR_ARG
  *                    and a message (nb_last_error(NULL))
  *   stream           cudaStream_t as void* (NULL = legacy default stream)
- * The call waits for `stream` before returning and reports a bounded-wait
- * timeout as NB_ERR_TIMEOUT. Its first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture. All calls share the one array, which
+ * The call waits for `stream` (only that stream) before returning and
+ * reports a bounded-wait timeout as NB_ERR_TIMEOUT. Its first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and keeps it for the process; make that first call
+ * before any stream capture, and do not use this entry point after a
+ * cudaDeviceReset of that device. All calls share the one array, which
  * keeps the previous call's contents (everything that is read is rewritten
  * first): calls that overlap on the GPU, from several host threads or on
  * several streams, race on it and must be serialised by the caller.

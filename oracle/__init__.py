@@ -199,9 +199,11 @@ class Oracle:
         return x, v, g
 
 
-    def leapfrog_grad(self, x0, v0, m, eps, dt, nsteps, xbar, vbar=None):
+    def leapfrog_grad(self, x0, v0, m, eps, dt, nsteps, xbar, vbar=None, on_vjp=None):
         """Gradients (dL/dx0, dL/dv0, dL/dm) of a loss L of the state after
         nsteps leapfrog steps, given xbar = dL/dx(T) and vbar = dL/dv(T).
+        on_vjp(x, ga), if given, sees the operands of every force VJP the
+        sweep takes (for error scales in tests; it changes nothing).
 
         Chain rule through the steps of `leapfrog` in reverse. One step maps
         (x, v, a) with a = Eq. (gravity) at x to
@@ -234,11 +236,15 @@ class Oracle:
         zero_p = np.zeros(n)
         for s in range(int(nsteps) - 1, -1, -1):
             ab_next = ab - 0.5 * dt * vb
+            if on_vjp is not None:
+                on_vjp(xs[s + 1], ab_next)
             gx, gm = self.force_vjp(xs[s + 1], m, eps, ab_next, zero_p)
             xb = xb + gx
             mb = mb + gm
             ab = -0.5 * dt * vb - 0.5 * dt * dt * xb
             vb = vb + dt * xb
+        if on_vjp is not None:
+            on_vjp(xs[0], ab)
         gx, gm = self.force_vjp(xs[0], m, eps, ab, zero_p)
         return xb + gx, vb, mb + gm
 

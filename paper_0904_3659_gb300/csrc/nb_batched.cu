@@ -153,14 +153,11 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPla
     }
 }
 
-// Pack cluster blockIdx.x (FP32 or FP64 source) into its padded slot. With
-// CENTRE (compensated mode, FP64 state) every particle is stored as the FP32
-// offset from the cluster's centroid, formed in FP64: all pairs of a batch
-// lie inside one cluster, so x_i - x_j is then independent of where the
-// cluster sits (no u |x| loss from rounding far-away positions).
+// Pack cluster blockIdx.x (FP32 or FP64 source, rounded to FP32) into its
+// padded slot.
 constexpr int kPackThreads = 256;
 
-template <typename T, bool CENTRE>
+template <typename T>
 __global__ void __launch_bounds__(kPackThreads) batch_pack_kernel(const T *__restrict__ x,
                                                                   const float *__restrict__ m,
                                                                   const int64_t *__restrict__ off,
@@ -169,29 +166,11 @@ __global__ void __launch_bounds__(kPackThreads) batch_pack_kernel(const T *__res
     const int64_t c = blockIdx.x;
     const int64_t o = off[c], po = poff[c], psz = poff[c + 1] - po;
     const int64_t nc = psz > 0 ? off[c + 1] - o : 0;
-    double cen[3] = {0.0, 0.0, 0.0};
-    if (CENTRE) {
-        __shared__ double s[3][kPackThreads];
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int64_t li = threadIdx.x; li < nc; li += kPackThreads)
-            for (int k = 0; k < 3; ++k) acc[k] += (double)x[3 * (o + li) + k];
-        for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int w = kPackThreads / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w)
-                for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
-            __syncthreads();
-        }
-        if (nc > 0)
-            for (int k = 0; k < 3; ++k) cen[k] = s[k][0] / (double)nc;
-    }
     for (int64_t li = threadIdx.x; li < psz; li += kPackThreads) {
         float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
         if (li < nc) {
             const int64_t i = o + li;
-            const float px = (float)((double)x[3 * i] - cen[0]);
-            const float py = (float)((double)x[3 * i + 1] - cen[1]);
-            const float pz = (float)((double)x[3 * i + 2] - cen[2]);
+            const float px = (float)x[3 * i], py = (float)x[3 * i + 1], pz = (float)x[3 * i + 2];
             const float hm = -0.5f * m[i];
             lo = make_float4(-px, -px, -py, -py);
             hi = make_float4(-pz, -pz, hm, hm);
@@ -202,6 +181,67 @@ __global__ void __launch_bounds__(kPackThreads) batch_pack_kernel(const T *__res
     }
 }
 
+// Compensated mode on FP64 state: cluster blockIdx.x as HL records (two
+// JParts per particle, see kHLRecords), relative to the centre of the
+// cluster's bounding box, on the grid 2^(E-23) set by the box's half-width
+// (all pairs lie inside one cluster, so each cluster has its own frame and
+// grid). Padding rows are inert (zero position and mass).
+__global__ void __launch_bounds__(kPackThreads) batch_pack_hl_kernel(const double *__restrict__ x,
+                                                                     const float *__restrict__ m,
+                                                                     const int64_t *__restrict__ off,
+                                                                     const int64_t *__restrict__ poff,
+                                                                     JPart *__restrict__ jp) {
+    __shared__ double s[6][kPackThreads];
+    const int64_t c = blockIdx.x;
+    const int t = threadIdx.x;
+    const int64_t o = off[c], po = poff[c], psz = poff[c + 1] - po;
+    const int64_t nc = psz > 0 ? off[c + 1] - o : 0;
+    if (psz <= 0) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t li = t; li < nc; li += kPackThreads)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], x[3 * (o + li) + k]);
+            hi[k] = fmax(hi[k], x[3 * (o + li) + k]);
+        }
+    for (int k = 0; k < 3; ++k) {
+        s[k][t] = lo[k];
+        s[3 + k][t] = hi[k];
+    }
+    __syncthreads();
+    for (int w = kPackThreads / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 3; ++k) {
+                s[k][t] = fmin(s[k][t], s[k][t + w]);
+                s[3 + k][t] = fmax(s[3 + k][t], s[3 + k][t + w]);
+            }
+        __syncthreads();
+    }
+    double cen[3], ext = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        cen[k] = 0.5 * (s[k][0] + s[3 + k][0]);
+        ext = fmax(ext, 0.5 * (s[3 + k][0] - s[k][0]));
+    }
+    const int e = hl_grid_exponent(ext);
+    const double g = ldexp(1.0, e - 23), ginv = ldexp(1.0, 23 - e);
+    for (int64_t li = t; li < psz; li += kPackThreads) {
+        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f}, hm = 0.f;
+        if (li < nc) {
+            const int64_t i = o + li;
+            for (int k = 0; k < 3; ++k) {
+                const double y = x[3 * i + k] - cen[k];
+                const double yh = rint(y * ginv) * g;  // exact: |y| <= 2^e
+                h[k] = (float)yh;
+                l[k] = (float)(y - yh);
+            }
+            hm = -0.5f * m[i];
+        }
+        float4 *dst = reinterpret_cast<float4 *>(jp + kHLRecords * (po + li));
+        dst[0] = make_float4(-h[0], -h[0], -h[1], -h[1]);
+        dst[1] = make_float4(-h[2], -h[2], hm, hm);
+        dst[2] = make_float4(-l[0], -l[0], -l[1], -l[1]);
+        dst[3] = make_float4(-l[2], -l[2], 0.f, 0.f);
+    }
+}
 
 struct BatchArgs {
     const JPart *jp;
@@ -221,17 +261,20 @@ struct StageMeta {
     int item, cluster, iblock, jt, end;
 };
 
+// HL: the particles are HL records (two JParts each, batch_pack_hl_kernel)
+// and each pair's x_i - x_j is formed by tile_pass_hl.
 // Warp-level persistent kernel: every warp of a CTA is an independent
 // worker with its own shared-memory stages, barriers and item stream. Lane 0
 // pops (cluster, i-block) items from the device queue, issues the 1-D bulk
 // copies of that cluster's j-tiles, and the whole warp consumes them. A work
 // item is 32 lanes x IPT i-particles (IPT/2 packed pairs per lane), so the
 // item equals the cluster padding and no CTA-wide barrier is needed.
-template <int WARPS, int IPT, int JT, int STAGES, bool COMP>
+template <int WARPS, int IPT, int JT, int STAGES, bool COMP, bool HL>
 __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArgs A) {
     constexpr int P = IPT / 2;
     constexpr int IB = 32 * IPT;
-    constexpr uint32_t TILE_BYTES = JT * sizeof(JPart);
+    constexpr int RS = HL ? kHLRecords : 1;  // JParts per particle
+    constexpr uint32_t TILE_BYTES = JT * RS * sizeof(JPart);
     static_assert(kClusterPad % IB == 0 && kClusterPad % JT == 0, "tiles must divide the padding");
     constexpr size_t WARP_BYTES = (size_t)STAGES * TILE_BYTES;
 
@@ -296,7 +339,8 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
         } else {
             issued_at[s] = kk;
             mbar_arrive_expect_tx(&full[s], TILE_BYTES);
-            bulk_g2s(tiles + (size_t)s * JT, A.jp + p_base + (int64_t)p_jt * JT, TILE_BYTES, &full[s]);
+            bulk_g2s(tiles + (size_t)s * JT * RS, A.jp + (p_base + (int64_t)p_jt * JT) * RS, TILE_BYTES,
+                     &full[s]);
             ++p_jt;
         }
     };
@@ -304,6 +348,7 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
         for (int kk = 0; kk < STAGES - 1; ++kk) produce(kk);
 
     float2 xi[P], yi[P], zi[P];
+    float2 lxi[P], lyi[P], lzi[P];  // HL: remainders of the i-particles' positions
     float2 sum[P][4], cmp[P][4];
     const float2 zero2 = splat2(0.f);
     int cur_item = -1, cur_cluster = 0, cur_b = 0;
@@ -349,13 +394,22 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
             for (int q = 0; q < P; ++q) {
                 int64_t i0 = base + (2 * q) * 32 + lane, i1 = i0 + 32;
                 if (!NB_IN(A.err, 12, i1 < A.cap_padded)) i0 = i1 = 0;
-                const float4 A0 = reinterpret_cast<const float4 *>(A.jp + i0)[0];
-                const float4 B0 = reinterpret_cast<const float4 *>(A.jp + i0)[1];
-                const float4 A1 = reinterpret_cast<const float4 *>(A.jp + i1)[0];
-                const float4 B1 = reinterpret_cast<const float4 *>(A.jp + i1)[1];
+                const float4 A0 = reinterpret_cast<const float4 *>(A.jp + i0 * RS)[0];
+                const float4 B0 = reinterpret_cast<const float4 *>(A.jp + i0 * RS)[1];
+                const float4 A1 = reinterpret_cast<const float4 *>(A.jp + i1 * RS)[0];
+                const float4 B1 = reinterpret_cast<const float4 *>(A.jp + i1 * RS)[1];
                 xi[q] = make_float2(-A0.x, -A1.x);
                 yi[q] = make_float2(-A0.z, -A1.z);
                 zi[q] = make_float2(-B0.x, -B1.x);
+                if (HL) {
+                    const float4 C0 = reinterpret_cast<const float4 *>(A.jp + i0 * RS + 1)[0];
+                    const float4 D0 = reinterpret_cast<const float4 *>(A.jp + i0 * RS + 1)[1];
+                    const float4 C1 = reinterpret_cast<const float4 *>(A.jp + i1 * RS + 1)[0];
+                    const float4 D1 = reinterpret_cast<const float4 *>(A.jp + i1 * RS + 1)[1];
+                    lxi[q] = make_float2(-C0.x, -C1.x);
+                    lyi[q] = make_float2(-C0.z, -C1.z);
+                    lzi[q] = make_float2(-D0.x, -D1.x);
+                }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     sum[q][r] = zero2;
@@ -363,7 +417,7 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                 }
             }
         }
-        const JPart *T = tiles + (size_t)s * JT;
+        const JPart *T = tiles + (size_t)s * JT * RS;
         float2 acc[P][4];
 #pragma unroll
         for (int q = 0; q < P; ++q)
@@ -377,11 +431,19 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                 self0[q] = ibase + (2 * q) * 32 + lane - jbase;
                 self1[q] = self0[q] + 32;
             }
-            tile_pass<P, JT, 1, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
-                                                                    self1);
+            if constexpr (HL)
+                tile_pass_hl<P, JT, 1, true, true>(T, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
+                                                   self1);
+            else
+                tile_pass<P, JT, 1, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2,
+                                                                        self0, self1);
         } else {
-            tile_pass<P, JT, 4, false, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2, self0,
-                                                                     self1);
+            if constexpr (HL)
+                tile_pass_hl<P, JT, 4, false, true>(T, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
+                                                    self1);
+            else
+                tile_pass<P, JT, 4, false, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2,
+                                                                         self0, self1);
         }
 #pragma unroll
         for (int q = 0; q < P; ++q)
@@ -488,37 +550,38 @@ __global__ void batch_kick_kernel(double *__restrict__ v, const float *__restric
 }
 
 // Registry of batched shapes.
-template <int W, int I, int J, int S, bool C>
+template <int W, int I, int J, int S, bool C, bool H>
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t st) {
-    batched_pair_kernel<W, I, J, S, C><<<grid, W * 32, smem, st>>>(a);
+    batched_pair_kernel<W, I, J, S, C, H><<<grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 struct BatchVariant {
     int threads, ipt, jtile, stages;
-    bool comp;
+    bool comp, hl;
     const void *kernel;
     size_t smem;
     cudaError_t (*launch)(const BatchArgs &, int, size_t, cudaStream_t);
 };
 
-template <int W, int S, int J>
+template <int W, int S, int J, int RS>
 constexpr size_t batch_smem() {
-    return (size_t)W * S * (J * sizeof(JPart) + sizeof(uint64_t) + sizeof(StageMeta) + sizeof(int));
+    return (size_t)W * S * (J * RS * sizeof(JPart) + sizeof(uint64_t) + sizeof(StageMeta) + sizeof(int));
 }
 
-// threads = warps x 32; ipt; jtile; stages
-#define NB_BVARIANT(W, I, J, S, C)                                                            \
-    {W * 32, I, J, S, C, (const void *)batched_pair_kernel<W, I, J, S, C>, batch_smem<W, S, J>(), \
-     launch_batched<W, I, J, S, C>}
+// threads = warps x 32; ipt; jtile; stages; compensated; HL records
+#define NB_BVARIANT(W, I, J, S, C, H)                                                           \
+    {W * 32, I, J, S, C, H, (const void *)batched_pair_kernel<W, I, J, S, C, H>,                  \
+     batch_smem<W, S, J, H ? kHLRecords : 1>(), launch_batched<W, I, J, S, C, H>}
 
 // One warp per CTA (up to 18 resident per SM, bounded by shared memory):
 // 0.902 against 0.943 ms per plain evaluation of 1024 clusters with 4 warps
 // per CTA (16 resident), the compensated mode unchanged (0.958 ms); 2 stages
 // or 4 were slower (GB300, one process, interleaved).
 static const BatchVariant kBatch[] = {
-    NB_BVARIANT(1, 4, 128, 3, false),
-    NB_BVARIANT(1, 4, 128, 3, true),
+    NB_BVARIANT(1, 4, 128, 3, false, false),
+    NB_BVARIANT(1, 4, 128, 3, true, false),
+    NB_BVARIANT(1, 4, 128, 3, true, true),  // compensated on FP64 state (HL records)
 };
 #undef NB_BVARIANT
 
@@ -567,8 +630,9 @@ int batch_resident(const BatchVariant &v, int sm_count) {
 }
 
 // Scratch for a batch, sized from (n_total, C) alone (offsets stay on the device).
-nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, BatchPlanHost *out) {
-    const BatchVariant &v = kBatch[comp ? 1 : 0];
+nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, bool hl,
+                        BatchPlanHost *out) {
+    const BatchVariant &v = kBatch[hl ? 2 : comp ? 1 : 0];
     const int ib = 32 * v.ipt;  // one warp per work item
     out->v = &v;
     out->n_total = n_total;
@@ -578,7 +642,9 @@ nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, Batc
         return fail(ctx, NB_ERR_ARG, "batch too large for 32-bit work items");
     out->grid = batch_resident(v, ctx_sm_count(ctx));
     nb_status st;
-    if ((st = bensure(ctx, B_JP, (size_t)out->cap_padded * sizeof(JPart))) != NB_OK) return st;
+    if ((st = bensure(ctx, B_JP, (size_t)out->cap_padded * (hl ? kHLRecords : 1) * sizeof(JPart))) !=
+        NB_OK)
+        return st;
     if ((st = bensure(ctx, B_POFF, (size_t)(C + 1) * sizeof(int64_t))) != NB_OK) return st;
     if ((st = bensure(ctx, B_ITEMS, (size_t)out->cap_items * sizeof(int4))) != NB_OK) return st;
     if ((st = bensure(ctx, B_NITEMS, 2 * sizeof(int))) != NB_OK) return st;  // count, queue head
@@ -671,9 +737,10 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchPlanHost h{};
-    if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
+    if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, false, &h)) != NB_OK)
+        return st;
     if ((st = batch_plan(ctx, offsets, eps, n_clusters, h, s)) != NB_OK) return st;
-    batch_pack_kernel<float, false><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
+    batch_pack_kernel<float><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
         x, m, offsets, static_cast<const int64_t *>(bslot(ctx, B_POFF)),
         static_cast<JPart *>(bslot(ctx, B_JP)));
     cudaError_t e = cudaGetLastError();
@@ -695,22 +762,21 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
         return fail(ctx, NB_ERR_ARG, "NULL array pointer");
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool hl = mode == NB_COMPENSATED;
     BatchPlanHost h{};
-    if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, &h)) != NB_OK) return st;
+    if ((st = batch_prepare(ctx, n_clusters, n_total, hl, hl, &h)) != NB_OK) return st;
     if ((st = batch_plan(ctx, offsets, eps, n_clusters, h, s)) != NB_OK) return st;
     const int64_t *poff = static_cast<const int64_t *>(bslot(ctx, B_POFF));
     JPart *jp = static_cast<JPart *>(bslot(ctx, B_JP));
     const unsigned nb3 = (unsigned)((3 * n_total + 255) / 256);
     cudaError_t e;
 
-    const bool centre = mode == NB_COMPENSATED;
     auto force = [&]() -> nb_status {
-        if (centre)
-            batch_pack_kernel<double, true><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
-                x, m, offsets, poff, jp);
+        if (hl)
+            batch_pack_hl_kernel<<<(unsigned)n_clusters, kPackThreads, 0, s>>>(x, m, offsets, poff, jp);
         else
-            batch_pack_kernel<double, false><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
-                x, m, offsets, poff, jp);
+            batch_pack_kernel<double><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(x, m, offsets,
+                                                                                   poff, jp);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(ctx, le, "batched pack launch");
         return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);

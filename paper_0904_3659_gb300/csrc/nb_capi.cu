@@ -202,10 +202,18 @@ const PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp) {
 nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *prepacked,
                     int64_t n, float eps, float *a, float *p, bool comp, cudaStream_t st) {
     const PairVariant *vp = &choose_variant(ctx, n, comp);
-    // Packed input (FP64 state packed by the caller): a shape that reads it.
-    if (prepacked && vp->tile.fused) vp = pair_variant(comp, pair_default_unfused_index(comp, n));
+    // Packed input (FP64 state packed by the caller), or no potential wanted
+    // (p NULL): a shape that reads packed particles.
+    if ((prepacked || !p) && vp->tile.fused) vp = pair_variant(comp, pair_default_unfused_index(comp, n));
+    // No potential wanted: the same shape without the potential term, if compiled.
+    if (!p)
+        if (const PairVariant *tw = no_pot_twin(*vp)) vp = tw;
+    PairPlan plan = make_plan(*vp, n, resident_ctas(ctx, *vp));
+    if (plan.grid == 0) {  // a shape that cannot serve n: the built-in packed one
+        vp = pair_variant(comp, pair_default_unfused_index(comp, n));
+        plan = make_plan(*vp, n, resident_ctas(ctx, *vp));
+    }
     const PairVariant &v = *vp;
-    const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
     cudaError_t e;
     if (v.tile.fused) {
         e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, plan.partial_bytes);
@@ -232,7 +240,7 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
         fa.p_scale = pot_scale(v.tile.refine);
         {
             TimedLaunch t(ctx, K_PAIR, st);
-            e = v.launch_fused(fa, plan.grid, v.smem, st);
+            e = v.launch_fused(fa, plan.grid, plan.smem, st);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "fused pair kernel launch");
         return NB_OK;
@@ -292,19 +300,22 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     return NB_OK;
 }
 
-nb_status reserve_frames(nb_ctx *ctx, int64_t n) {
-    const PairVariant &v = *frames_variant(n);
-    const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
-    cudaError_t e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, plan.partial_bytes);
+nb_status reserve_hl(nb_ctx *ctx, int64_t n) {
+    size_t bytes = 0;
+    for (bool no_pot : {false, true}) {
+        const PairVariant &v = *hl_variant(n, no_pot);
+        bytes = std::max(bytes, make_plan(v, n, resident_ctas(ctx, v)).partial_bytes);
+    }
+    cudaError_t e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (partial sums)");
     return NB_OK;
 }
 
-nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, const int32_t *perm,
-                           int64_t n, float eps, float *a, float *p, cudaStream_t st) {
-    const PairVariant &v = *frames_variant(n);
+nb_status run_force_hl(nb_ctx *ctx, const JPart *jp, int64_t n, float eps, float *a, float *p,
+                       cudaStream_t st) {
+    const PairVariant &v = *hl_variant(n, p == nullptr);
     const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
-    nb_status rs = reserve_frames(ctx, n);
+    nb_status rs = reserve_hl(ctx, n);
     if (rs != NB_OK) return rs;
     PairArgs pa{};
     pa.jp = jp;
@@ -317,7 +328,6 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
     pa.eps2 = eps * eps;
     pa.fault_unit = ctx->fault_unit;
     pa.wait_ns = ctx->wait_ns;
-    pa.cref = cref;
     pa.npad = plan.npad;
     pa.partial_len = (int64_t)(ctx->partial_bytes / sizeof(float4));
     cudaError_t e;
@@ -325,7 +335,7 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
         TimedLaunch t(ctx, K_PAIR, st);
         e = v.launch(pa, plan.grid, v.smem, st);
     }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "pair kernel launch (frames)");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pair kernel launch (HL)");
     ReduceArgs ra{};
     ra.partial = pa.partial;
     ra.a = a;
@@ -336,7 +346,6 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
     ra.grid = plan.grid;
     ra.maxseg = plan.maxseg;
     ra.ib = plan.ib;
-    ra.perm = perm;
     ra.a_scale = accel_scale(v.tile.refine);
     ra.p_scale = pot_scale(v.tile.refine);
     ra.partial_len = pa.partial_len;
@@ -345,7 +354,7 @@ nb_status run_force_frames(nb_ctx *ctx, const JPart *jp, const float4 *cref, con
         TimedLaunch t(ctx, K_REDUCE, st);
         e = launch_reduce(ra, true, st);
     }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch (frames)");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch (HL)");
     return NB_OK;
 }
 
@@ -457,13 +466,18 @@ nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode) {
     const bool comp = mode == NB_COMPENSATED;
     size_t jp = 0, part = 0;
     int64_t nib = 0;
-    // Every shape this context might pick for n: reserve for the largest.
+    // Every shape this context might pick for n (and the shapes' twins
+    // without the potential): reserve for the largest.
     for (int k = 0; k < pair_variant_count(comp); ++k) {
-        const PairVariant &v = *pair_variant(comp, k);
-        const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
-        jp = std::max(jp, (size_t)plan.npad * sizeof(JPart));
-        part = std::max(part, plan.partial_bytes);
-        if (v.tile.fused) nib = std::max(nib, plan.nib);
+        const PairVariant *cands[2] = {pair_variant(comp, k), no_pot_twin(*pair_variant(comp, k))};
+        for (const PairVariant *vp : cands) {
+            if (!vp) continue;
+            const PairPlan plan = make_plan(*vp, n, resident_ctas(ctx, *vp));
+            if (plan.grid == 0) continue;  // the shape cannot serve n
+            jp = std::max(jp, (size_t)plan.npad * sizeof(JPart));
+            part = std::max(part, plan.partial_bytes);
+            if (vp->tile.fused) nib = std::max(nib, plan.nib);
+        }
     }
     cudaError_t e = ensure_buffer(&ctx->d_jp, &ctx->jp_bytes, jp);
     if (e == cudaSuccess) e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, part);
@@ -637,8 +651,10 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_til
     std::vector<float> best_ms_of(nv, 0.f);
     std::vector<int> order;  // the shapes timed
     for (int k = 0; st == NB_OK && k < nv; ++k) {
-        // Single-launch shapes: small n only.
+        // Single-launch shapes: small n only, and only those that can serve n.
         if (pair_variant(comp, k)->tile.fused && !fused_candidate(n)) continue;
+        if (make_plan(*pair_variant(comp, k), n, resident_ctas(ctx, *pair_variant(comp, k))).grid == 0)
+            continue;
         order.push_back(k);
         ctx->has_override[mi] = true;
         ctx->override_idx[mi] = k;

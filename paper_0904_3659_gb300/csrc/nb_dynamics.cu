@@ -18,7 +18,6 @@
 #include "nb_device.cuh"
 #include "nb_ext.h"
 #include "nb_internal.h"
-#include "nb_order.h"
 
 namespace nbk {
 
@@ -70,8 +69,8 @@ __global__ void kick_drift_pack_kernel(double *__restrict__ x, double *__restric
     pack_one(jp, i, xn[0], xn[1], xn[2], m[i]);
 }
 
-// Kicks and drift without packing (the compensated path packs offsets from
-// reference points in a separate kernel).
+// Kicks and drift without packing (the compensated path packs HL records
+// in a separate kernel).
 __global__ void kick_drift_kernel(double *__restrict__ x, double *__restrict__ v,
                                   const float *__restrict__ a, int64_t n, double dt, int kick_back) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -148,6 +147,94 @@ __global__ void adj_first_fold_kernel(double *__restrict__ lx, double *__restric
     if (k < n) lm[k] = lm[k] + (double)gm[k];
 }
 
+// HL packing of FP64 positions (compensated mode). Bounding box: per-block
+// min/max, then one block combines them (min and max do not depend on the
+// order) and forms the frame {centre x, y, z, grid G = 2^(E-23)} with 2^E
+// bounding every |x - centre| (hl_grid_exponent).
+constexpr int kBoxThreads = 256;
+
+__global__ void __launch_bounds__(kBoxThreads) hl_box_partial_kernel(const double *__restrict__ x,
+                                                                    int64_t n,
+                                                                    double *__restrict__ part) {
+    __shared__ double s[6][kBoxThreads];
+    const int t = threadIdx.x;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)kBoxThreads + t; i < n; i += (int64_t)gridDim.x * kBoxThreads)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], x[3 * i + c]);
+            hi[c] = fmax(hi[c], x[3 * i + c]);
+        }
+    for (int c = 0; c < 3; ++c) {
+        s[c][t] = lo[c];
+        s[3 + c][t] = hi[c];
+    }
+    __syncthreads();
+    for (int w = kBoxThreads / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int c = 0; c < 3; ++c) {
+                s[c][t] = fmin(s[c][t], s[c][t + w]);
+                s[3 + c][t] = fmax(s[3 + c][t], s[3 + c][t + w]);
+            }
+        __syncthreads();
+    }
+    if (t < 6) part[6 * blockIdx.x + t] = s[t][0];
+}
+
+__global__ void __launch_bounds__(kBoxThreads) hl_frame_kernel(const double *__restrict__ part,
+                                                              int nblocks, double *__restrict__ frame) {
+    __shared__ double s[6][kBoxThreads];
+    const int t = threadIdx.x;
+    double b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int k = t; k < nblocks; k += kBoxThreads)
+        for (int c = 0; c < 3; ++c) {
+            b[c] = fmin(b[c], part[6 * k + c]);
+            b[3 + c] = fmax(b[3 + c], part[6 * k + 3 + c]);
+        }
+    for (int c = 0; c < 6; ++c) s[c][t] = b[c];
+    __syncthreads();
+    for (int w = kBoxThreads / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int c = 0; c < 3; ++c) {
+                s[c][t] = fmin(s[c][t], s[c][t + w]);
+                s[3 + c][t] = fmax(s[3 + c][t], s[3 + c][t + w]);
+            }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double ext = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            frame[c] = 0.5 * (s[c][0] + s[3 + c][0]);
+            ext = fmax(ext, 0.5 * (s[3 + c][0] - s[c][0]));
+        }
+        frame[3] = ldexp(1.0, hl_grid_exponent(ext) - 23);
+    }
+}
+
+// Particle i as HL records relative to the frame: h = y rounded to the grid
+// (exact in FP32: |y| <= 2^E), l = fl32(y - h); rows n..npad-1 are inert.
+__global__ void hl_pack_kernel(const double *__restrict__ x, const float *__restrict__ m, int64_t n,
+                               int64_t npad, const double *__restrict__ frame,
+                               JPart *__restrict__ jp) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f}, hm = 0.f;
+    if (i < n) {
+        const double g = frame[3], ginv = 1.0 / g;  // a power of two: exact
+        for (int c = 0; c < 3; ++c) {
+            const double y = x[3 * i + c] - frame[c];
+            const double yh = rint(y * ginv) * g;
+            h[c] = (float)yh;
+            l[c] = (float)(y - yh);
+        }
+        hm = -0.5f * m[i];
+    }
+    float4 *dst = reinterpret_cast<float4 *>(jp + kHLRecords * i);
+    dst[0] = make_float4(-h[0], -h[0], -h[1], -h[1]);
+    dst[1] = make_float4(-h[2], -h[2], hm, hm);
+    dst[2] = make_float4(-l[0], -l[0], -l[1], -l[1]);
+    dst[3] = make_float4(-l[2], -l[2], 0.f, 0.f);
+}
+
 // Energy: per-block sums of K = 1/2 m |v|^2 and W = -1/2 m p in a fixed
 // tree order, then one block adds the block sums in order.
 constexpr int kEnergyThreads = 256;
@@ -202,7 +289,7 @@ enum Slot : int {
     S_P = SLOT_P,
     S_EBLK = SLOT_ENERGY_BLK,
     S_EOUT = SLOT_ENERGY_OUT,
-    S_PERM = SLOT_FRAMES,
+    S_BOX = SLOT_HL_BOX,
     S_ADJ = SLOT_ADJOINT
 };
 
@@ -217,45 +304,41 @@ nb_status ensure_slot(nb_ctx *ctx, int k, size_t bytes) {
 
 unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// Reserve everything one force evaluation from packed FP64 positions needs.
+// Reserve everything one force evaluation from packed FP64 positions needs
+// (HL records, two JParts per particle, in compensated mode).
 nb_status reserve_force(nb_ctx *ctx, int64_t n, bool comp) {
     const PairVariant &v = choose_variant(ctx, n, comp);
     const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
-    return ensure_slot(ctx, S_JP, (size_t)plan.npad * sizeof(JPart));
+    return ensure_slot(ctx, S_JP, (size_t)plan.npad * (comp ? kHLRecords : 1) * sizeof(JPart));
 }
 
 int64_t padded(int64_t n) { return round_up(std::max<int64_t>(n, 1), kPad); }
 
-// Compensated path for FP64 state: permutation (Morton order) and, per force
-// evaluation, reference-point offsets. One buffer holds the permutation, the
-// ordering scratch and the reference points.
-struct Frames {
-    int32_t *perm = nullptr;
-    void *order_scratch = nullptr;
-    float4 *cref = nullptr;
-};
+// Compensated path for FP64 state: each force evaluation packs HL records
+// relative to the centre of the current bounding box (box partials, then one
+// block that forms the frame, then the pack), so the grid always covers
+// every particle however far the integrator has moved it.
+int box_blocks(int64_t n) { return (int)std::min<int64_t>(1024, (n + kBoxThreads - 1) / kBoxThreads); }
 
-nb_status reserve_frames_state(nb_ctx *ctx, int64_t n, Frames *f) {
-    const size_t perm_bytes = round_up((int64_t)order_pow2(n) * sizeof(int32_t), 256);
-    const size_t order_bytes = round_up((int64_t)order_scratch_bytes(n), 256);
-    const size_t cref_bytes = (size_t)(padded(n) / 256) * sizeof(float4);
-    nb_status st = ensure_slot(ctx, S_PERM, perm_bytes + order_bytes + cref_bytes);
+nb_status reserve_hl_state(nb_ctx *ctx, int64_t n) {
+    nb_status st = ensure_slot(ctx, S_BOX, (size_t)(box_blocks(n) * 6 + 4) * sizeof(double));
     if (st != NB_OK) return st;
-    if ((st = reserve_frames(ctx, n)) != NB_OK) return st;
-    unsigned char *base = static_cast<unsigned char *>(slot(ctx, S_PERM));
-    f->perm = reinterpret_cast<int32_t *>(base);
-    f->order_scratch = base + perm_bytes;
-    f->cref = reinterpret_cast<float4 *>(base + perm_bytes + order_bytes);
-    return NB_OK;
+    return reserve_hl(ctx, n);
 }
 
-// Eq. (gravity) from FP64 positions through the frames (order already set).
-nb_status force_frames(nb_ctx *ctx, const double *x, const float *m, const Frames &f, int64_t n,
-                       float eps, float *a, float *p, cudaStream_t st) {
+// Eq. (gravity) from FP64 positions through HL records (p may be NULL).
+nb_status force_hl(nb_ctx *ctx, const double *x, const float *m, int64_t n, float eps, float *a,
+                   float *p, cudaStream_t st) {
     JPart *jp = static_cast<JPart *>(slot(ctx, S_JP));
-    cudaError_t e = launch_frames_pack(x, m, f.perm, n, padded(n), 256, jp, f.cref, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "frames pack launch");
-    return run_force_frames(ctx, jp, f.cref, f.perm, n, eps, a, p, st);
+    double *part = static_cast<double *>(slot(ctx, S_BOX));
+    double *frame = part + 6 * box_blocks(n);
+    const int nblk = box_blocks(n);
+    hl_box_partial_kernel<<<nblk, kBoxThreads, 0, st>>>(x, n, part);
+    hl_frame_kernel<<<1, kBoxThreads, 0, st>>>(part, nblk, frame);
+    hl_pack_kernel<<<blocks_for(padded(n), 256), 256, 0, st>>>(x, m, n, padded(n), frame, jp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "HL pack launch");
+    return run_force_hl(ctx, jp, n, eps, a, p, st);
 }
 
 // Enqueue the steps 1 .. nsteps-1 body: fused kicks+drift+pack, force.
@@ -278,19 +361,16 @@ nb_status record(nb_ctx *ctx, double *x_hist, int t, const double *x, int64_t n,
     return e == cudaSuccess ? NB_OK : cuda_fail(ctx, e, "position history copy");
 }
 
-// The compensated leap-frog: the order is fixed for the call (from the entry
-// positions); every force evaluation re-packs offsets from the tiles'
-// reference points. Steps after the first are replayed from a graph, unless
-// the positions of every step are recorded (x_hist).
-nb_status leapfrog_frames(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
-                          int64_t n, float eps, double dt, int nsteps, int a_valid, cudaStream_t s,
-                          double *x_hist) {
-    Frames f;
-    nb_status st = reserve_frames_state(ctx, n, &f);
+// The compensated leap-frog: every force evaluation packs the FP64 positions
+// as HL records (force_hl). Steps after the first are replayed from a graph,
+// unless the positions of every step are recorded (x_hist).
+nb_status leapfrog_hl(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
+                      int64_t n, float eps, double dt, int nsteps, int a_valid, cudaStream_t s,
+                      double *x_hist) {
+    nb_status st = reserve_hl_state(ctx, n);
     if (st != NB_OK) return st;
-    cudaError_t e = launch_spatial_order(x, n, f.order_scratch, f.perm, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "ordering launch");
-    if (!a_valid && (st = force_frames(ctx, x, m, f, n, eps, a, p, s)) != NB_OK) return st;
+    cudaError_t e;
+    if (!a_valid && (st = force_hl(ctx, x, m, n, eps, a, p, s)) != NB_OK) return st;
     if ((st = record(ctx, x_hist, 0, x, n, s)) != NB_OK) return st;
     if (nsteps == 0) return NB_OK;
     const unsigned nb3 = blocks_for(3 * n, 256);
@@ -298,7 +378,7 @@ nb_status leapfrog_frames(nb_ctx *ctx, double *x, double *v, const float *m, flo
         kick_drift_kernel<<<nb3, 256, 0, s>>>(x, v, a, n, dt, kick_back);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(ctx, le, "leap-frog update launch");
-        return force_frames(ctx, x, m, f, n, eps, a, p, s);
+        return force_hl(ctx, x, m, n, eps, a, p, s);
     };
     if ((st = step(0)) != NB_OK || (st = record(ctx, x_hist, 1, x, n, s)) != NB_OK) return st;
     const int rest = nsteps - 1;
@@ -392,18 +472,12 @@ nb_status leapfrog_plain(nb_ctx *ctx, double *x, double *v, const float *m, floa
     return NB_OK;
 }
 
-// Scratch of a leap-frog call (before any graph capture); *pbuf receives the
-// potential array to use (the caller's, else the context's).
-nb_status reserve_leapfrog(nb_ctx *ctx, int64_t n, nb_mode mode, float *p, float **pbuf) {
+// Scratch of a leap-frog call (before any graph capture). Without a caller's
+// potential array (p NULL) the force kernels sum a_i only.
+nb_status reserve_leapfrog(nb_ctx *ctx, int64_t n, nb_mode mode) {
     nb_status st;
     if ((st = reserve_force(ctx, n, mode == NB_COMPENSATED)) != NB_OK) return st;
-    if ((st = nb_reserve(ctx, n, mode)) != NB_OK) return st;
-    *pbuf = p;
-    if (!p) {
-        if ((st = ensure_slot(ctx, S_P, (size_t)n * sizeof(float))) != NB_OK) return st;
-        *pbuf = static_cast<float *>(slot(ctx, S_P));
-    }
-    return NB_OK;
+    return nb_reserve(ctx, n, mode);
 }
 
 }  // namespace
@@ -423,11 +497,10 @@ nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, fl
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Scratch first (allocation never happens inside the captured graph).
-    float *pbuf = nullptr;
-    if ((st = reserve_leapfrog(ctx, n, mode, p, &pbuf)) != NB_OK) return st;
+    if ((st = reserve_leapfrog(ctx, n, mode)) != NB_OK) return st;
     if (mode == NB_COMPENSATED)
-        return leapfrog_frames(ctx, x, v, m, a, pbuf, n, eps, dt, nsteps, a_valid, s, nullptr);
-    return leapfrog_plain(ctx, x, v, m, a, pbuf, n, eps, dt, nsteps, a_valid, s, nullptr);
+        return leapfrog_hl(ctx, x, v, m, a, p, n, eps, dt, nsteps, a_valid, s, nullptr);
+    return leapfrog_plain(ctx, x, v, m, a, p, n, eps, dt, nsteps, a_valid, s, nullptr);
 }
 
 nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, const float *a,
@@ -451,10 +524,9 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t b_xv = al(n3 * sizeof(double)), b_hist = al((size_t)(nsteps + 1) * n3 * sizeof(double));
     const size_t b_v3 = al(n3 * sizeof(float)), b_s = al((size_t)n * sizeof(float));
-    const size_t total = 2 * b_xv + b_hist + 4 * b_v3 + 2 * b_s;
+    const size_t total = 2 * b_xv + b_hist + 4 * b_v3 + b_s;
     if ((st = ensure_slot(ctx, S_ADJ, total)) != NB_OK) return st;
-    float *pbuf = nullptr;
-    if ((st = reserve_leapfrog(ctx, n, mode, nullptr, &pbuf)) != NB_OK) return st;
+    if ((st = reserve_leapfrog(ctx, n, mode)) != NB_OK) return st;
     unsigned char *base = static_cast<unsigned char *>(slot(ctx, S_ADJ));
     double *xw = reinterpret_cast<double *>(base);
     double *vw = reinterpret_cast<double *>(base + b_xv);
@@ -464,17 +536,16 @@ nb_status nb_leapfrog_adjoint(nb_ctx *ctx, const double *x, const double *v, con
     float *ga32 = x32 + b_v3 / sizeof(float);
     float *gx32 = ga32 + b_v3 / sizeof(float);
     float *gm32 = gx32 + b_v3 / sizeof(float);
-    float *pw = gm32 + b_s / sizeof(float);
 
-    // Replay the segment on copies with the forward's own kernels (same
-    // order and reference frames, so the same positions), recording x.
+    // Replay the segment on copies with the forward's own kernels (so the
+    // same positions), recording x.
     cudaError_t e = cudaMemcpyAsync(xw, x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(vw, v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && a) e = cudaMemcpyAsync(aw, a, n3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint replay copies");
     st = mode == NB_COMPENSATED
-             ? leapfrog_frames(ctx, xw, vw, m, aw, pw, n, eps, dt, nsteps, a != nullptr, s, hist)
-             : leapfrog_plain(ctx, xw, vw, m, aw, pw, n, eps, dt, nsteps, a != nullptr, s, hist);
+             ? leapfrog_hl(ctx, xw, vw, m, aw, nullptr, n, eps, dt, nsteps, a != nullptr, s, hist)
+             : leapfrog_plain(ctx, xw, vw, m, aw, nullptr, n, eps, dt, nsteps, a != nullptr, s, hist);
     if (st != NB_OK) return st;
 
     // Reverse sweep, last step first: one VJP of Eq. (gravity) per step.
@@ -523,11 +594,8 @@ nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *
     float *pbuf = static_cast<float *>(slot(ctx, S_P));
     cudaError_t e;
     if (comp) {
-        Frames f;
-        if ((st = reserve_frames_state(ctx, n, &f)) != NB_OK) return st;
-        e = launch_spatial_order(x, n, f.order_scratch, f.perm, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "ordering launch");
-        if ((st = force_frames(ctx, x, m, f, n, eps, abuf, pbuf, s)) != NB_OK) return st;
+        if ((st = reserve_hl_state(ctx, n)) != NB_OK) return st;
+        if ((st = force_hl(ctx, x, m, n, eps, abuf, pbuf, s)) != NB_OK) return st;
     } else {
         pack_f64_kernel<<<blocks_for(padded(n), 256), 256, 0, s>>>(x, m, n, padded(n), jp);
         e = cudaGetLastError();

@@ -14,7 +14,7 @@ namespace nbx {
 enum ExtSlot : int {
     SLOT_FP64_JP = 0,   // packed particles from FP64 state (leap-frog, energy)
     SLOT_ENERGY_A,      // accelerations computed by nb_energy
-    SLOT_P,             // potentials when the caller passes none
+    SLOT_P,             // potentials computed by nb_energy
     SLOT_ENERGY_BLK,    // energy block sums
     SLOT_ENERGY_OUT,    // energy result
     SLOT_BATCH_JP,      // padded packed clusters
@@ -25,7 +25,7 @@ enum ExtSlot : int {
     SLOT_BATCH_IBASE,   // first item of each cluster
     SLOT_VJP_VP,        // packed VJP records
     SLOT_VJP_PART,      // VJP partial sums
-    SLOT_FRAMES,        // permutation, ordering scratch, reference points
+    SLOT_HL_BOX,        // bounding-box partials of FP64 positions (HL packing)
     SLOT_ADJOINT,       // leap-frog adjoint: replayed state, position history, VJP operands
     SLOT_COUNT
 };
@@ -72,14 +72,13 @@ cudaError_t ensure_buffer(void **ptr, size_t *cap, size_t bytes);
 int resident_ctas(nb_ctx *ctx, const nbk::PairVariant &v);
 const nbk::PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp);
 
-// Frame path (compensated, FP64 state): pair kernel on particles packed in
-// perm order as offsets from per-tile reference points cref, combine
-// scattering result k to particle perm[k].
-nb_status run_force_frames(nb_ctx *ctx, const nbk::JPart *jp, const float4 *cref,
-                           const int32_t *perm, int64_t n, float eps, float *a, float *p,
-                           cudaStream_t st);
-// Allocate the frame path's partial sums for n (before any graph capture).
-nb_status reserve_frames(nb_ctx *ctx, int64_t n);
+// Compensated path on FP64 state: pair kernel on HL records (two JParts per
+// particle, nbk::kHLRecords), then the compensated combine; p may be NULL
+// (the potential is then not summed).
+nb_status run_force_hl(nb_ctx *ctx, const nbk::JPart *jp, int64_t n, float eps, float *a, float *p,
+                       cudaStream_t st);
+// Allocate the HL path's partial sums for n (before any graph capture).
+nb_status reserve_hl(nb_ctx *ctx, int64_t n);
 
 // pack (unless prepacked) -> pair -> combine, enqueued on st.
 nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const nbk::JPart *prepacked,

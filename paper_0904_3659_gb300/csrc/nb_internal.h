@@ -2,6 +2,7 @@
 // kernel translation units. Not installed; not part of the public ABI.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -19,6 +20,31 @@ struct alignas(32) JPart {
     float2 nx, ny, nz, hm;
 };
 static_assert(sizeof(JPart) == 32, "JPart must be 32 bytes");
+
+// Positions held in FP64 (the integrator's state) enter the compensated
+// kernels as two FP32 words per coordinate (HL records, two JParts per
+// particle): relative to a reference point c of the system (or cluster),
+// y = x - c is split into h = y rounded to the grid G = 2^(E-23), where
+// 2^E bounds every |y|, and l = fl32(y - h). Every h is a multiple of G
+// below 2^23 G in magnitude, so h_i - h_j is exact in FP32, and the pair
+// kernel forms x_i - x_j as (h_i - h_j) + (l_i - l_j) with a single
+// rounding that matters. Record 2k: (-h, -h, ..., -m/2, -m/2); record
+// 2k+1: (-l_x, -l_x, -l_y, -l_y, -l_z, -l_z, 0, 0).
+constexpr int kHLRecords = 2;
+
+// The grid exponent E for a system whose positions relative to its
+// reference point are bounded by `extent` (>= 0): the smallest E with
+// |y| <= 2^E (at least -100, so that G stays a normal FP32 number).
+__host__ __device__ inline int hl_grid_exponent(double extent) {
+    int e = -100;
+    if (extent > 0.0) {
+        int ex = 0;
+        const double f = frexp(extent, &ex);  // extent = f 2^ex, f in [0.5, 1)
+        e = f == 0.5 ? ex - 1 : ex;
+        if (e < -100) e = -100;
+    }
+    return e;
+}
 
 // Particle arrays are padded to a multiple of this (>= every i-block and
 // j-tile size) with inert entries (m = 0 at the origin).
@@ -40,8 +66,7 @@ struct PairArgs {
     float eps2;            // eps^2 in FP32
     int64_t fault_unit;    // test hook: unit whose copy is never issued (-1: none)
     uint64_t wait_ns;      // limit of one bounded barrier wait
-    const float4 *cref;    // per-j-tile reference points (frame variants only)
-    int64_t npad;          // entries of jp (bounds checks of the debug build)
+    int64_t npad;          // particles in jp (bounds checks of the debug build)
     int64_t partial_len;   // float4 entries of partial (debug build)
 };
 
@@ -72,14 +97,13 @@ struct FusedArgs {
 struct ReduceArgs {
     const float4 *partial;
     float *a;              // [n][3]
-    float *p;              // [n]
+    float *p;              // [n], or nullptr: the potential is not written
     int64_t n;
     int64_t njt;
     int64_t units;
     int grid;
     int maxseg;
     int ib;
-    const int32_t *perm;   // if set, result k is written to particle perm[k]
     float a_scale;         // sums -> a_i and p_i: accel_scale / pot_scale of
     float p_scale;         //   the pair variant's refine setting
     int64_t partial_len;   // float4 entries of partial (debug build)
@@ -100,7 +124,7 @@ __host__ __device__ constexpr float accel_scale(int refine) { return refine ? 0.
 __host__ __device__ constexpr float pot_scale(int refine) { return refine ? 1.0f : -2.0f; }
 
 // Newton steps of the built-in default shapes and of the fixed-shape kernels
-// (batched, frames, allocation-free): none, since on sm_103a the step does
+// (batched, HL, allocation-free): none, since on sm_103a the step does
 // not improve the FP32 result (see nb_tile.refine).
 constexpr int kDefaultRefine = 0;
 
@@ -115,9 +139,12 @@ struct PairVariant {
 };
 
 // Registry of compiled variants (nb_pair.cu).
-// Frame variants: compensated kernels that re-centre on per-tile reference
-// points (positions packed as offsets, see nb_order.cu).
-const PairVariant *frames_variant(int64_t n);
+// HL variants: compensated kernels on HL records (positions from FP64 state,
+// see kHLRecords); no_pot selects the twin that sums a_i only.
+const PairVariant *hl_variant(int64_t n, bool no_pot = false);
+// The twin of a plain packed shape that sums a_i only (12 FP32 operations
+// per pair), or nullptr if that shape has none.
+const PairVariant *no_pot_twin(const PairVariant &v);
 int pair_variant_count(bool comp);
 const PairVariant *pair_variant(bool comp, int idx);
 int pair_default_index(bool comp, int64_t n);
@@ -134,10 +161,13 @@ cudaError_t launch_reduce(const ReduceArgs &r, bool comp, cudaStream_t st);
 cudaError_t launch_fill_uniform(float *x, float *m, int64_t n, uint64_t seed, cudaStream_t st);
 
 // Work decomposition of one nb_force call for a given variant.
+// grid == 0: the shape cannot serve this n (the warp-level fused form
+// outside its size range); the caller picks another.
 struct PairPlan {
     int64_t n, npad, nib, njt, units, nchunks;
     int grid, maxseg, ib, words;
     size_t partial_bytes;
+    size_t smem;  // dynamic shared memory of the launch
     int64_t partial_len() const { return (int64_t)(partial_bytes / sizeof(float4)); }
 };
 PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas);

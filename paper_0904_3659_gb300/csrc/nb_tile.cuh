@@ -26,6 +26,8 @@ using namespace nbdev;
 // (same IEEE round-to-nearest operations, so every mask gives bit-identical
 // results). Mixing trades issue slots (packed: one per two lanes) against
 // the lower sustained pipe rate of packed instructions.
+// POT = false leaves the potential out (acc[q][3] untouched): 12 FP32
+// operations per pair, for callers that need only a_i (the integrator).
 enum : int { kMixD = 1, kMixS = 2, kMixN = 4, kMixQ = 8, kMixW = 16, kMixA = 32, kMixAll = 63 };
 
 template <bool PK>
@@ -41,7 +43,7 @@ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
     return PK ? fma2(a, b, c) : make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
 }
 
-template <int P, int JT, int UNR, bool DIAG, int MIX, bool NEWTON>
+template <int P, int JT, int UNR, bool DIAG, int MIX, bool NEWTON, bool POT = true>
 __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const float2 (&xi)[P],
                                           const float2 (&yi)[P], const float2 (&zi)[P],
                                           float2 (&acc)[P][4], const float2 eps2,
@@ -78,12 +80,61 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
                 if (jj == self1[q]) hm.y = 0.f;
             }
             const float2 qv = vmul<PQ>(hm, u);
-            acc[q][3] = vadd<PQ>(acc[q][3], qv);
+            if (POT) acc[q][3] = vadd<PQ>(acc[q][3], qv);
             const float2 u2 = vmul<PW>(u, u);
             const float2 w = vmul<PW>(qv, u2);
             acc[q][0] = vfma<PA>(w, dx, acc[q][0]);
             acc[q][1] = vfma<PA>(w, dy, acc[q][1]);
             acc[q][2] = vfma<PA>(w, dz, acc[q][2]);
+        }
+    }
+}
+
+// The same pass for positions held as two FP32 words (HL records, see
+// JPart): particle k occupies T[2k] = (-h, -h, ..., -m/2, -m/2) and
+// T[2k+1] = (-l, -l, ...), with h on a power-of-two grid fine enough that
+// h_i - h_j is exact in FP32 and l = x - h the FP32 remainder. Each
+// component of x_i - x_j is then (h_i - h_j) + (l_i - l_j): one rounding of
+// the exact difference (up to the remainders' own rounding, far below it),
+// so close pairs keep their relative accuracy wherever they sit. 6 FP32
+// operations per pair more than tile_pass (19, or 18 without the potential).
+template <int P, int JT, int UNR, bool DIAG, bool POT>
+__device__ __forceinline__ void tile_pass_hl(const JPart *__restrict__ T, const float2 (&xi)[P],
+                                             const float2 (&yi)[P], const float2 (&zi)[P],
+                                             const float2 (&lxi)[P], const float2 (&lyi)[P],
+                                             const float2 (&lzi)[P], float2 (&acc)[P][4],
+                                             const float2 eps2, const int (&self0)[P],
+                                             const int (&self1)[P]) {
+#pragma unroll UNR
+    for (int jj = 0; jj < JT; ++jj) {
+        const float4 A = reinterpret_cast<const float4 *>(T + 2 * jj)[0];
+        const float4 B = reinterpret_cast<const float4 *>(T + 2 * jj)[1];
+        const float4 C = reinterpret_cast<const float4 *>(T + 2 * jj + 1)[0];
+        const float4 D = reinterpret_cast<const float4 *>(T + 2 * jj + 1)[1];
+        const float2 nxj = make_float2(A.x, A.y), nyj = make_float2(A.z, A.w);
+        const float2 nzj = make_float2(B.x, B.y), hmj = make_float2(B.z, B.w);
+        const float2 nlxj = make_float2(C.x, C.y), nlyj = make_float2(C.z, C.w);
+        const float2 nlzj = make_float2(D.x, D.y);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float2 dx = add2(add2(xi[q], nxj), add2(lxi[q], nlxj));
+            const float2 dy = add2(add2(yi[q], nyj), add2(lyi[q], nlyj));
+            const float2 dz = add2(add2(zi[q], nzj), add2(lzi[q], nlzj));
+            float2 s = fma2(dx, dx, eps2);
+            s = fma2(dy, dy, s);
+            s = fma2(dz, dz, s);
+            const float2 u = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
+            float2 hm = hmj;
+            if (DIAG) {
+                if (jj == self0[q]) hm.x = 0.f;
+                if (jj == self1[q]) hm.y = 0.f;
+            }
+            const float2 qv = mul2(hm, u);
+            if (POT) acc[q][3] = add2(acc[q][3], qv);
+            const float2 w = mul2(qv, mul2(u, u));
+            acc[q][0] = fma2(w, dx, acc[q][0]);
+            acc[q][1] = fma2(w, dy, acc[q][1]);
+            acc[q][2] = fma2(w, dz, acc[q][2]);
         }
     }
 }

@@ -179,10 +179,10 @@ def test_batched_leapfrog_matches_single_cluster_calls(nb, ctx):
 
 def test_batched_compensated_fp64_state_far_from_origin(nb, ctx, oracle_mod):
     # Clusters placed far from the origin (FP64 state): the compensated batch
-    # packs offsets from each cluster's centroid, so its error no longer
-    # depends on where the cluster sits (plain rounding of |x| ~ 1e3 loses
-    # u |x|); what remains is the rounding of the offsets inside the cluster's
-    # own frame, the floor a centred system has (a few 1e-6 at these sizes).
+    # splits each position, relative to its cluster's bounding-box centre,
+    # into an exact FP32 grid part and an FP32 remainder, so x_i - x_j carries
+    # one rounding wherever the cluster sits (plain rounding of |x| ~ 1e3
+    # loses u |x|). Target of the compensated path: 1e-6.
     import torch
     dev = torch.device("cuda:0")
     sizes = [900, 2500, 300]
@@ -217,5 +217,45 @@ def test_batched_compensated_fp64_state_far_from_origin(nb, ctx, oracle_mod):
             w = max(w, (np.linalg.norm(A[lo:hi] - ra, axis=1) / ramag).max(),
                     (np.abs(P[lo:hi] - rp) / rp).max())
         worst[mode] = w
-    assert worst[1] <= 5e-6, worst
+    assert worst[1] <= 1e-6, worst
     assert worst[1] * 100 <= worst[0], worst
+
+
+@pytest.mark.parametrize("shift", [0.0, 300.0])
+def test_batched_compensated_kdk_clusters_against_oracle(nb, ctx, oracle_mod, shift):
+    # The compensated batched leap-frog on FP64 state (each cluster's
+    # positions as grid part + remainder): after 8 graph-replayed KDK steps the force it
+    # returns at the final positions matches the FP64 oracle at those same
+    # positions within 1e-6 for every particle of every cluster, centred or
+    # moved away from the origin; two runs give the same bits.
+    import torch
+    dev = torch.device("cuda:0")
+    cl = workloads.clusters(96, seed=7, nmin=32, nmax=2048)
+    x0 = cl.x + shift * np.array([1.0, -0.5, 0.25])
+    m32 = cl.m.astype(np.float32)
+    eps32 = cl.eps.astype(np.float32)
+    n, C = x0.shape[0], len(cl.sizes)
+    stream = torch.cuda.Stream()
+    runs = []
+    for _ in range(2):
+        xt = torch.from_numpy(x0.copy()).to(dev)
+        vt = torch.from_numpy(cl.v.copy()).to(dev)
+        mt = torch.from_numpy(m32).to(dev)
+        ot = torch.from_numpy(cl.offsets).to(dev)
+        et = torch.from_numpy(eps32).to(dev)
+        a = torch.zeros((n, 3), device=dev)
+        p = torch.zeros(n, device=dev)
+        torch.cuda.synchronize()
+        nb.nb_leapfrog_batched_step(ctx, xt, vt, mt, ot, C, n, et, a, p, 1.0 / 256, 8, 0, 1, stream)
+        nb.nb_synchronize(ctx, stream)
+        runs.append((xt.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy()))
+    (x1, a1, p1), (x2, a2, p2) = runs
+    assert x1.tobytes() == x2.tobytes() and a1.tobytes() == a2.tobytes()
+    assert p1.tobytes() == p2.tobytes()
+    worst = 0.0
+    for c in range(C):
+        lo, hi = cl.offsets[c], cl.offsets[c + 1]
+        ra, rp, ramag = oracle_mod.force(x1[lo:hi], m32[lo:hi], eps32[c])
+        worst = max(worst, (np.linalg.norm(a1[lo:hi].astype(np.float64) - ra, axis=1) / ramag).max(),
+                    (np.abs(p1[lo:hi] - rp) / rp).max())
+    assert worst <= 1e-6, worst

@@ -2,9 +2,10 @@
 computed-index access of the kernels against its buffer and records a
 violation instead of making it. A selection of parity tests that exercises
 every kernel (single system plain and compensated, every tile shape, ragged
-sizes, batches with empty and invalid clusters, FP64 state with reference
-frames, the adjoint, the allocation-free entry point) runs against that
-build in a fresh process: any violation fails the test that saw it."""
+sizes, batches with empty and invalid clusters, FP64 state with positions
+split into grid part and remainder, the adjoint, the allocation-free entry
+point) runs against that build in a fresh process: any violation fails the
+test that saw it."""
 import os
 import subprocess
 import sys
@@ -23,6 +24,7 @@ def test_parity_selection_under_bounds_checks():
     lib = build.build(debug=True)
     env = dict(os.environ, NB_LIBRARY=lib)
     sel = ("ragged or every_tile or coincident or uneven or invalid or far_from_origin or "
+           "compensated_kdk or final_force or "
            "zero_steps or fp64_state or vjp_matches_oracle or noalloc")
     files = ["tests/test_force_parity.py", "tests/test_batched_parity.py",
              "tests/test_leapfrog_parity.py", "tests/test_vjp_parity.py",

@@ -182,27 +182,46 @@ def _force_from_fp64(nb, ctx, stream, x64, m, eps, mode):
 
 
 @pytest.mark.parametrize("offset", [0.0, 1000.0])
-def test_fp64_state_force_compensated_frames(nb, ctx, stream, oracle_mod, offset):
+def test_fp64_state_force_compensated_hl(nb, ctx, stream, oracle_mod, offset):
     # Positions held in FP64, the cluster centred at the origin or displaced
     # to x = 1000. Rounding them to FP32 (plain) costs u |x| absolute in every
-    # x_i - x_j; the compensated path packs offsets from per-tile reference
-    # points of a spatially ordered copy and stays within 1e-6 of the FP64
-    # oracle evaluated on the unrounded positions.
+    # x_i - x_j; the compensated path splits each position (relative to the
+    # bounding box's centre) into an exact FP32 grid part and an FP32
+    # remainder, so every x_i - x_j carries one rounding, and it stays within
+    # 1e-6 of the FP64 oracle on the unrounded positions for every particle.
     n, eps = 65536, np.float32(1.0 / 128)
     x, _, m = workloads.plummer(n, seed=21)
     x = x + np.array([offset, 0.0, 0.0])
     m = m.astype(np.float32)
-    rows = workloads.sample_rows(n, 600, seed=4)
-    ra, rp, ramag = oracle_mod.force_rows(x, m, eps, rows)
+    ra, rp, ramag = oracle_mod.force(x, m, eps)
     errs = {}
     for mode in (0, 1):
         a, p = _force_from_fp64(nb, ctx, stream, x, m, eps, mode)
-        ea = np.linalg.norm(a[rows] - ra, axis=1) / ramag
-        ep = np.abs(p[rows] - rp) / rp
+        ea = np.linalg.norm(a - ra, axis=1) / ramag
+        ep = np.abs(p - rp) / rp
         errs[mode] = max(ea.max(), ep.max())
     assert errs[1] <= 1e-6, errs
     if offset:
-        assert errs[0] > 1e-5, errs   # the rounding loss the frames remove
+        assert errs[0] > 1e-5, errs   # the rounding loss the compensated path removes
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_leapfrog_final_force_all_rows(nb, ctx, stream, oracle_mod, mode):
+    # After 16 graph-replayed KDK steps (N = 8192 Plummer, eps = 1/128), the
+    # force the integrator returns at its final FP64 positions against the
+    # FP64 oracle at those positions, every particle: 1e-5 plain, 1e-6
+    # compensated.
+    n, eps, dt = 8192, np.float32(1.0 / 128), 1.0 / 256
+    x0, v0, m = plummer_state(n, 24)
+    s = State(x0, v0, m)
+    s.step(nb, ctx, eps, dt, 16, 0, mode, stream)
+    x1, _ = s.numpy()
+    ra, rp, ramag = oracle_mod.force(x1, m, eps)
+    a = s.a.cpu().numpy().astype(np.float64)
+    p = s.p.cpu().numpy().astype(np.float64)
+    ea = (np.linalg.norm(a - ra, axis=1) / ramag).max()
+    ep = (np.abs(p - rp) / rp).max()
+    assert max(ea, ep) <= (1e-6 if mode else 1e-5), (ea, ep)
 
 
 def test_compensated_leapfrog_deterministic_and_close_to_plain(nb, ctx, stream):

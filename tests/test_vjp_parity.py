@@ -234,14 +234,38 @@ def _trajectory_grad_check(nb, ctx, oracle_mod, n, eps, dt, steps, ncoords, seed
              "m": mt.grad.cpu().numpy().astype(np.float64)}
 
     xT64, _, _ = oracle_mod.leapfrog(x0, v0, m, eps, dt, steps)
-    ref = dict(zip("xvm", oracle_mod.leapfrog_grad(x0, v0, m, eps, dt, steps, 2 * (xT64 - y))))
-    # Every coordinate: FP32 rounding in strongly cancelling sums leaves a few
-    # outliers (a mass gradient whose terms nearly cancel), so the bound is on
-    # the 99.9th percentile (1e-4) and on the maximum (1e-3).
+    sweep = []  # operands of every force VJP of the oracle's reverse sweep
+    ref = dict(zip("xvm", oracle_mod.leapfrog_grad(x0, v0, m, eps, dt, steps, 2 * (xT64 - y),
+                                                   on_vjp=lambda xs, ga: sweep.append((xs, ga)))))
+    # Every coordinate, relative to max(|ref|, 1e-3 max |ref|), within 1e-4.
+    # A mass gradient dL/dm_k = sum over the sweep's VJPs of
+    # sum_l -(r_kl . ga_l) s_kl^{-3/2} can cancel to far below its terms; its
+    # FP32 rounding error is then set by the size of those terms, not by the
+    # result. A mass coordinate beyond 1e-4 is accepted only if its error is
+    # within 1e-5 of that magnitude, M_k = sum over the VJPs and l of
+    # |r_kl . ga_l| s_kl^{-3/2} (the scale the VJP kernel's own check uses).
+    e2 = float(np.float32(eps)) ** 2
     for kind in "xvm":
         r = ref[kind]
         rel = np.abs(grads[kind] - r) / np.maximum(np.abs(r), 1e-3 * np.abs(r).max())
-        assert np.percentile(rel, 99.9) <= 1e-4 and rel.max() <= 1e-3, (kind, rel.max())
+        k = int(np.argmax(rel))
+        print(f"{kind}: every-coordinate max {rel.max():.3e} at flat index {k} "
+              f"(ref {r.flat[k]:.3e}, gpu {grads[kind].flat[k]:.3e}), p99.9 {np.percentile(rel, 99.9):.3e}")
+        if kind != "m":
+            assert rel.max() <= 1e-4, (kind, rel.max())
+            continue
+        for k in np.flatnonzero(rel > 1e-4):
+            M = 0.0
+            for xs, ga in sweep:
+                d = xs[k] - xs
+                s2 = (d * d).sum(1) + e2
+                term = np.abs((d * ga).sum(1)) * s2 ** -1.5
+                term[k] = 0.0
+                M += term.sum()
+            cond = abs(grads["m"][k] - r[k]) / M
+            print(f"m[{k}]: {rel[k]:.3e} relative, {cond:.3e} of its term magnitude {M:.3e} "
+                  f"(|dL/dm| = {abs(r[k]):.3e})")
+            assert cond <= 1e-5, (k, rel[k], cond)
 
     def L(xx, vv, mm):
         xT_, _, _ = oracle_mod.leapfrog(xx, vv, mm, eps, dt, steps)
@@ -285,8 +309,8 @@ def test_trajectory_gradient_small(nb, ctx, oracle_mod):
 
 
 def test_trajectory_gradient_small_compensated(nb, ctx, oracle_mod):
-    # The same with the compensated force (per-tile reference frames in the
-    # forward and in the adjoint's replay).
+    # The same with the compensated force (positions as grid part + remainder
+    # in the forward and in the adjoint's replay).
     _trajectory_grad_check(nb, ctx, oracle_mod, 512, np.float32(1.0 / 64), 1.0 / 512, 64, 6, 5,
                            mode=1)
 
@@ -343,14 +367,56 @@ def test_library_adjoint_matches_autograd_composition(nb, ctx, every):
     np.testing.assert_allclose(gml, gma, rtol=1e-4, atol=1e-5 * np.abs(gma).max())
 
 
+ADJOINT_FD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                          "adjoint_fd_plummer16384.txt")
+
+
+def _read_adjoint_fd():
+    rows = []
+    with open(ADJOINT_FD) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, i, c, h, fd, g = line.split()
+            rows.append((k, int(i), int(c), float(h), float(fd), float(g)))
+    return rows
+
+
 def test_trajectory_gradient_plummer16384(nb, ctx, oracle_mod):
-    # The full workload (N = 16384, eps = 1/64, 64 steps of dt = 1/512,
-    # checkpoints every 8): each FP64 oracle trajectory takes seconds, so 3
-    # coordinates by default; NB_FULL_ADJOINT_CHECK=1 checks all 32.
+    # The differentiation workload (N = 16384 Plummer, eps = 1/64, 64 KDK
+    # steps of dt = 1/512, checkpoints every 8, L = sum |x(T) - y|^2): the
+    # library's gradient against FP64 central finite differences of the
+    # oracle's trajectory on all 32 stored coordinates (written by
+    # tests/golden/make_adjoint_fd.py from the oracle alone; recomputing
+    # them takes minutes), within 1e-4 relative, and on every coordinate
+    # against the oracle's FP64 reverse-mode gradient (_trajectory_grad_check
+    # with no live differences). NB_FULL_ADJOINT_CHECK=1 also recomputes the
+    # 32 differences live.
+    import torch
+    from paper_0904_3659_gb300.autograd import leapfrog
     w = workloads.WORKLOADS["plummer16384_adjoint64"]
-    ncoords = w["fd_coords"] if os.environ.get("NB_FULL_ADJOINT_CHECK") else 3
-    _trajectory_grad_check(nb, ctx, oracle_mod, w["n"], np.float32(w["eps"]), w["dt"], w["steps"],
-                           ncoords, w["seed"])
+    n, eps = w["n"], np.float32(w["eps"])
+    x0, v0, m = workloads.plummer(n, seed=w["seed"])
+    y = workloads.targets(x0, seed=w["target_seed"])
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
+    vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
+    mt = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
+    xT, _ = leapfrog(xt, vt, mt, eps, w["dt"], w["steps"], checkpoint_every=w["checkpoint"],
+                     nbctx=ctx)
+    ((xT - torch.from_numpy(y).to(dev)) ** 2).sum().backward()
+    g = {"x": xt.grad.cpu().numpy(), "v": vt.grad.cpu().numpy(), "m": mt.grad.cpu().numpy()}
+    rows = _read_adjoint_fd()
+    assert len(rows) == w["fd_coords"]
+    worst = 0.0
+    for kind, i, c, h, fd, _ in rows:
+        v = float(g[kind][i] if kind == "m" else g[kind][i, c])
+        err = abs(v - fd) / abs(fd)
+        worst = max(worst, err)
+        assert err <= 1e-4, (kind, i, c, v, fd, err)
+    print(f"32 stored FD coordinates: worst relative error {worst:.3e}")
+    ncoords = w["fd_coords"] if os.environ.get("NB_FULL_ADJOINT_CHECK") else 0
+    _trajectory_grad_check(nb, ctx, oracle_mod, n, eps, w["dt"], w["steps"], ncoords, w["seed"])
 
 
 def test_checkpointing_does_not_change_gradients(nb, ctx):
