@@ -57,13 +57,14 @@ def alu_peak(sm_count, sm_mhz, ops) -> float:
     return sm_count * sm_mhz * 1e6 * FP32_LANES_PER_SM / ops / 1e9
 
 
-# DRAM bytes (read + write) of one launch of the plain pair kernel, from an
-# ncu capture of that kernel alone on a Plummer sphere of N = 131072
-# (4.257 MB read, 0 written). The kernel reads each j-tile from
-# L2 after its first touch, so DRAM traffic grows with N, not N^2; the bench
-# reports it scaled to its N, and null for any other tile shape.
-PROFILED_TILE = (128, 12, 256, 3, 4, 1, 0, 1, 63, 0, 0)
-PROFILED_DRAM_BYTES, PROFILED_N = 4.257e6, 131072
+# DRAM bytes (read + write) of one launch of the large-N plain pair kernel
+# (256 threads x 4 i, 1024-particle tiles), from an ncu capture of that
+# kernel alone on a Plummer sphere of N = 131072 (4.215 MB read, 0 written).
+# The kernel reads each j-tile from L2 after its first touch, so DRAM traffic
+# grows with N, not N^2; the bench reports it scaled to its N, and null for
+# any other tile shape.
+PROFILED_TILE = (256, 4, 1024, 3, 4, 1, 0, 0, 63, 0, 0)
+PROFILED_DRAM_BYTES, PROFILED_N = 4.215e6, 131072
 
 
 # --------------------------------------------------------------------------

@@ -133,15 +133,28 @@ def library():
     return _lib
 
 
+_DTYPES = {}
+
+
+def _torch_dtype(name: str):
+    dt = _DTYPES.get(name)
+    if dt is None:
+        import torch
+        dt = _DTYPES[name] = getattr(torch, name)
+    return dt
+
+
 def _dev(t, dtype: str, numel: int, name: str) -> Optional[int]:
     """Address of a device array argument, checked: a torch tensor must have
     the dtype the C signature takes, be contiguous, hold at least `numel`
     elements and live on a CUDA device (an int is taken as a raw address,
     None as NULL). A wrong tensor raises here instead of being read as
-    something else by the kernels."""
+    something else by the kernels. (Kept to a few attribute reads: it runs
+    on every call, and at small n the host time per call is what a loop of
+    calls sees.)"""
     if t is None or isinstance(t, int):
         return t
-    if str(t.dtype) != "torch." + dtype:
+    if t.dtype is not _torch_dtype(dtype):
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
@@ -161,15 +174,27 @@ def _addr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+_raw_stream = None
+
+
 def _stream(stream) -> Optional[int]:
+    """cudaStream_t for a call: the given stream (a torch stream or a raw
+    handle), else torch's current stream of the current device, read as a
+    raw handle without building a Stream object."""
+    global _raw_stream
     if stream is None:
-        try:
-            import torch
-            if torch.cuda.is_available():
-                return torch.cuda.current_stream().cuda_stream or None
-        except ImportError:
-            pass
-        return None
+        if _raw_stream is None:
+            try:
+                import torch
+                if not torch.cuda.is_available():
+                    return None
+                raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+                cur = torch.cuda.current_device
+                _raw_stream = ((lambda: raw(cur())) if raw is not None
+                               else (lambda: torch.cuda.current_stream().cuda_stream))
+            except ImportError:
+                return None
+        return _raw_stream() or None
     if isinstance(stream, int):
         return stream or None
     return stream.cuda_stream or None

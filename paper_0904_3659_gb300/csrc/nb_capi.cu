@@ -208,12 +208,8 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     // No potential wanted: the same shape without the potential term, if compiled.
     if (!p)
         if (const PairVariant *tw = no_pot_twin(*vp)) vp = tw;
-    PairPlan plan = make_plan(*vp, n, resident_ctas(ctx, *vp));
-    if (plan.grid == 0) {  // a shape that cannot serve n: the built-in packed one
-        vp = pair_variant(comp, pair_default_unfused_index(comp, n));
-        plan = make_plan(*vp, n, resident_ctas(ctx, *vp));
-    }
     const PairVariant &v = *vp;
+    const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
     cudaError_t e;
     if (v.tile.fused) {
         e = ensure_buffer(&ctx->d_partial, &ctx->partial_bytes, plan.partial_bytes);
@@ -294,7 +290,7 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     ra.err = ctx->d_err;
     {
         TimedLaunch t(ctx, K_REDUCE, st);
-        e = launch_reduce(ra, comp, st);
+        e = launch_reduce(ra, v.comp, st);  // the combine matches the kernel's running sums
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch");
     return NB_OK;
@@ -473,7 +469,6 @@ nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode) {
         for (const PairVariant *vp : cands) {
             if (!vp) continue;
             const PairPlan plan = make_plan(*vp, n, resident_ctas(ctx, *vp));
-            if (plan.grid == 0) continue;  // the shape cannot serve n
             jp = std::max(jp, (size_t)plan.npad * sizeof(JPart));
             part = std::max(part, plan.partial_bytes);
             if (vp->tile.fused) nib = std::max(nib, plan.nib);
@@ -651,10 +646,8 @@ nb_status nb_autotune(nb_ctx *ctx, int64_t n, nb_mode mode, void *stream, nb_til
     std::vector<float> best_ms_of(nv, 0.f);
     std::vector<int> order;  // the shapes timed
     for (int k = 0; st == NB_OK && k < nv; ++k) {
-        // Single-launch shapes: small n only, and only those that can serve n.
+        // Single-launch shapes: small n only.
         if (pair_variant(comp, k)->tile.fused && !fused_candidate(n)) continue;
-        if (make_plan(*pair_variant(comp, k), n, resident_ctas(ctx, *pair_variant(comp, k))).grid == 0)
-            continue;
         order.push_back(k);
         ctx->has_override[mi] = true;
         ctx->override_idx[mi] = k;

@@ -161,8 +161,6 @@ cudaError_t launch_reduce(const ReduceArgs &r, bool comp, cudaStream_t st);
 cudaError_t launch_fill_uniform(float *x, float *m, int64_t n, uint64_t seed, cudaStream_t st);
 
 // Work decomposition of one nb_force call for a given variant.
-// grid == 0: the shape cannot serve this n (the warp-level fused form
-// outside its size range); the caller picks another.
 struct PairPlan {
     int64_t n, npad, nib, njt, units, nchunks;
     int grid, maxseg, ib, words;

@@ -414,12 +414,46 @@ __global__ void reduce_kernel(const ReduceArgs r) {
 // Every addition order is fixed by the launch shape, so results are
 // bit-reproducible; there are no waits on other CTAs.
 constexpr int kFusedJmax = 1024;  // particles per shared-memory block (32 KB)
-// Warp-level form: sizes it serves (n < kWkMaxN) and the shared memory it
-// may ask for: 8 warps x a j stretch of up to 440 particles, then the
-// warps' compensated sums for two i-blocks of 128.
-constexpr int64_t kWkMaxN = (int64_t)1 << 13;
-constexpr int kWkStretchMax = 440;
-constexpr size_t kWkSmemMax = 8 * kWkStretchMax * sizeof(JPart) + 8 * 2 * 2 * 128 * sizeof(float4);
+
+// Load particles j0 .. j0 + cnt - 1 (cnt <= kFusedJmax) from x, m and pack
+// them into blk; rows at or beyond n are inert (m = 0 at the origin). Each
+// thread issues the loads of up to 4 particles before any of their stores,
+// so the block costs about one L2 round trip instead of four.
+template <int THREADS>
+__device__ __forceinline__ void pack_block(const float *__restrict__ x, const float *__restrict__ m,
+                                           int64_t n, int64_t j0, int cnt, JPart *__restrict__ blk) {
+    constexpr int R = 4;
+    for (int k0 = 0; k0 < cnt; k0 += R * THREADS) {
+        float4 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = k0 + r * THREADS + (int)threadIdx.x;
+            const int64_t j = j0 + k;
+            v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < cnt && j < n) v[r] = make_float4(x[3 * j], x[3 * j + 1], x[3 * j + 2], m[j]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = k0 + r * THREADS + (int)threadIdx.x;
+            if (k >= cnt) continue;
+            float4 *dst = reinterpret_cast<float4 *>(blk + k);
+            const float hm = -0.5f * v[r].w;
+            dst[0] = make_float4(-v[r].x, -v[r].x, -v[r].y, -v[r].y);
+            dst[1] = make_float4(-v[r].z, -v[r].z, hm, hm);
+        }
+    }
+}
+
+// Programmatic dependent launch of the single-launch kernels: they are
+// launched with programmatic stream serialization, so the next launch on the
+// stream can be scheduled while this one runs; a kernel waits for its
+// predecessor's completion (and memory) before it reads anything, and
+// releases its own dependents at once (they too wait for its completion
+// before reading). Without such a launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait_then_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs args) {
@@ -438,6 +472,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs
     JPart *blk = reinterpret_cast<JPart *>(smem);
     float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after the last block
     __shared__ int s_last;
+    pdl_wait_then_release();
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = args.n, nch = args.nchunks;
@@ -466,15 +501,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs
     for (int64_t bt0 = t0; bt0 < t1; bt0 += TPB) {
         const int64_t bt1 = bt0 + TPB < t1 ? bt0 + TPB : t1;
         const int cnt = (int)(bt1 - bt0) * JT;
-        for (int k = tid; k < cnt; k += THREADS) {
-            const int64_t j = bt0 * JT + k;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond n: inert (m = 0 at the origin)
-            if (j < n) v = make_float4(args.x[3 * j], args.x[3 * j + 1], args.x[3 * j + 2], args.m[j]);
-            float4 *dst = reinterpret_cast<float4 *>(blk + k);
-            const float hm = -0.5f * v.w;
-            dst[0] = make_float4(-v.x, -v.x, -v.y, -v.y);
-            dst[1] = make_float4(-v.z, -v.z, hm, hm);
-        }
+        pack_block<THREADS>(args.x, args.m, n, bt0 * JT, cnt, blk);
         __syncthreads();
         for (int64_t t = bt0 + warp; t < bt1; t += WARPS) {
             const JPart *T = blk + (t - bt0) * JT;
@@ -609,6 +636,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
     JPart *blk = reinterpret_cast<JPart *>(smem);
     float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after a segment's last block
     __shared__ int s_last;
+    pdl_wait_then_release();
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = args.n, njt = args.njt;
@@ -641,15 +669,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
         for (int64_t bt0 = t0; bt0 < t1; bt0 += TPB) {
             const int64_t bt1 = bt0 + TPB < t1 ? bt0 + TPB : t1;
             const int cnt = (int)(bt1 - bt0) * JT;
-            for (int k = tid; k < cnt; k += THREADS) {
-                const int64_t j = bt0 * JT + k;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond n: inert (m = 0 at the origin)
-                if (j < n) v = make_float4(args.x[3 * j], args.x[3 * j + 1], args.x[3 * j + 2], args.m[j]);
-                float4 *dst = reinterpret_cast<float4 *>(blk + k);
-                const float hm = -0.5f * v.w;
-                dst[0] = make_float4(-v.x, -v.x, -v.y, -v.y);
-                dst[1] = make_float4(-v.z, -v.z, hm, hm);
-            }
+            pack_block<THREADS>(args.x, args.m, n, bt0 * JT, cnt, blk);
             __syncthreads();
             for (int64_t t = bt0 + warp; t < bt1; t += WARPS) {
                 const JPart *T = blk + (t - bt0) * JT;
@@ -760,261 +780,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
     }
 }
 
-// ---------------------------------------------------------------------------
-// Warp-level stream-K form of the fused kernel (tile field fused = 3), for
-// small n: the flattened work (i-block b of IB = 32 IPT particles, particle
-// j), nib * n units in all, is split into equal contiguous ranges, one per
-// WARP of the grid (one CTA per SM), so every warp does the same number of
-// interactions to within one, whatever n is. A warp's range covers at most
-// two i-blocks (the host keeps nib <= warps). Each warp
-//  * packs its own j-particles (one or two contiguous pieces of x, m) into a
-//    private stretch of shared memory, all loads issued before any use;
-//  * for each i-block it touches, holds that block's i-particles (IPT/2
-//    packed pairs per lane) and sums its j-range in chunks of JT particles
-//    (a chunk partial, then the running sum; Kahan for COMP), the j == i
-//    term masked in the part of the range that holds the block's own
-//    particles.
-// The warps' sums are then added per i-block in warp order through shared
-// memory (the j stretch is reused), the CTA writes one partial per i-block
-// in pair_kernel's layout (maxseg 2) and counts itself in; the last CTA of
-// an i-block adds the partials in CTA order and writes a_i, p_i. Every order
-// is fixed by the launch shape (bit-reproducible); no CTA waits on another.
-// args.units = nib * n, args.njt = n (units per i-block), args.nchunks = the
-// j stretch per warp in particles.
-template <int P, int UNR, bool DIAG>
-__device__ __forceinline__ void range_pass(const JPart *__restrict__ T, int len, int jglob,
-                                           const float2 (&xi)[P], const float2 (&yi)[P],
-                                           const float2 (&zi)[P], float2 (&acc)[P][4],
-                                           const float2 eps2, const int64_t (&i0)[P]) {
-#pragma unroll UNR
-    for (int jj = 0; jj < len; ++jj) {
-        const float4 A = reinterpret_cast<const float4 *>(T + jj)[0];
-        const float4 B = reinterpret_cast<const float4 *>(T + jj)[1];
-        const float2 nxj = make_float2(A.x, A.y), nyj = make_float2(A.z, A.w);
-        const float2 nzj = make_float2(B.x, B.y);
-        const float2 hmj = make_float2(B.z, B.w);
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const float2 dx = add2(xi[q], nxj), dy = add2(yi[q], nyj), dz = add2(zi[q], nzj);
-            float2 s = fma2(dx, dx, eps2);
-            s = fma2(dy, dy, s);
-            s = fma2(dz, dz, s);
-            const float2 u = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
-            float2 hm = hmj;
-            if (DIAG) {
-                const int64_t j = jglob + jj;
-                if (j == i0[q]) hm.x = 0.f;
-                if (j == i0[q] + 32) hm.y = 0.f;
-            }
-            const float2 qv = mul2(hm, u);
-            acc[q][3] = add2(acc[q][3], qv);
-            const float2 w = mul2(qv, mul2(u, u));
-            acc[q][0] = fma2(w, dx, acc[q][0]);
-            acc[q][1] = fma2(w, dy, acc[q][1]);
-            acc[q][2] = fma2(w, dz, acc[q][2]);
-        }
-    }
-}
-
-template <int WARPS, int IPT, int JT, int UNR, int MINB, bool COMP>
-__global__ void __launch_bounds__(WARPS * 32, MINB) fused_wk_kernel(const FusedArgs args) {
-    static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
-    static_assert(kDefaultRefine == 0, "the warp-level form has no Newton step");
-    constexpr int THREADS = WARPS * 32;
-    constexpr int P = IPT / 2;
-    constexpr int IB = 32 * IPT;
-    constexpr int W = COMP ? 2 : 1;
-    static_assert(kPad % IB == 0, "i-blocks must divide the padding");
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t n = args.n, total = args.units, stretch = args.nchunks;
-    const int64_t G = (int64_t)args.grid * WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
-    const int64_t r0 = gw * total / G, r1 = (gw + 1) * total / G;
-    JPart *mine = reinterpret_cast<JPart *>(smem) + (int64_t)warp * stretch;
-    float4 *red = reinterpret_cast<float4 *>(smem + (size_t)WARPS * stretch * sizeof(JPart));  // [WARPS][2][W][IB]
-    __shared__ int s_last;
-    __shared__ int s_blk[WARPS][2];  // i-block of each warp segment (-1: none)
-
-    // The warp's segments: block b0 over [ja0, jb0), then possibly b0 + 1
-    // over [0, jb1).
-    const int64_t b0 = r0 / n;
-    const int64_t ja0 = r0 - b0 * n;
-    const int64_t jb0 = r1 - b0 * n < n ? r1 - b0 * n : n;
-    const int64_t jb1 = r1 > (b0 + 1) * n ? r1 - (b0 + 1) * n : 0;
-    const int len0 = (int)(jb0 - ja0 > 0 ? jb0 - ja0 : 0), len1 = (int)jb1;
-    const int cnt = len0 + len1;
-
-    // Pack the warp's j-particles (both pieces) into its stretch: the loads of
-    // up to 4 particles per lane are issued before their stores.
-    if (NB_IN(args.err, 35, cnt <= stretch)) {
-        for (int k0 = 0; k0 < cnt; k0 += 4 * 32) {
-            float4 v[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int k = k0 + r * 32 + lane;
-                v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < cnt) {
-                    const int64_t j = k < len0 ? ja0 + k : (int64_t)(k - len0);
-                    v[r] = make_float4(args.x[3 * j], args.x[3 * j + 1], args.x[3 * j + 2], args.m[j]);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int k = k0 + r * 32 + lane;
-                if (k < cnt) {
-                    float4 *dst = reinterpret_cast<float4 *>(mine + k);
-                    const float hm = -0.5f * v[r].w;
-                    dst[0] = make_float4(-v[r].x, -v[r].x, -v[r].y, -v[r].y);
-                    dst[1] = make_float4(-v[r].z, -v[r].z, hm, hm);
-                }
-            }
-        }
-    }
-    __syncwarp();
-
-    const float2 eps2 = splat2(args.eps2);
-    const float2 zero2 = splat2(0.f);
-
-    for (int sg = 0; sg < 2; ++sg) {
-        const int len = sg == 0 ? len0 : len1;
-        if (lane == 0) s_blk[warp][sg] = len > 0 ? (int)(b0 + sg) : -1;
-        if (len > 0) {
-            float2 sum[P][4], cmp[P][4];
-#pragma unroll
-            for (int q = 0; q < P; ++q)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) sum[q][r] = cmp[q][r] = zero2;
-            const int64_t b = b0 + sg, ja = sg == 0 ? ja0 : 0;
-            const JPart *T = mine + (sg == 0 ? 0 : len0);
-            float2 xi[P], yi[P], zi[P];
-            int64_t i0[P];
-#pragma unroll
-            for (int q = 0; q < P; ++q) {
-                i0[q] = b * IB + (2 * q) * 32 + lane;
-                const int64_t i1 = i0[q] + 32;
-                float3 p0 = make_float3(0.f, 0.f, 0.f), p1 = p0;
-                if (i0[q] < n) p0 = make_float3(args.x[3 * i0[q]], args.x[3 * i0[q] + 1], args.x[3 * i0[q] + 2]);
-                if (i1 < n) p1 = make_float3(args.x[3 * i1], args.x[3 * i1 + 1], args.x[3 * i1 + 2]);
-                xi[q] = make_float2(p0.x, p1.x);
-                yi[q] = make_float2(p0.y, p1.y);
-                zi[q] = make_float2(p0.z, p1.z);
-            }
-            // [ja, ja + len) in chunks of JT; the chunk holding the block's
-            // own particles [b IB, b IB + IB) runs masked.
-            const int64_t dlo = b * IB, dhi = dlo + IB;
-            for (int c0 = 0; c0 < len; c0 += JT) {
-                const int cl = len - c0 < JT ? len - c0 : JT;
-                const int64_t jg = ja + c0;
-                float2 acc[P][4];
-#pragma unroll
-                for (int q = 0; q < P; ++q)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
-                if (jg < dhi && dlo < jg + cl)
-                    range_pass<P, 1, true>(T + c0, cl, (int)jg, xi, yi, zi, acc, eps2, i0);
-                else
-                    range_pass<P, UNR, false>(T + c0, cl, (int)jg, xi, yi, zi, acc, eps2, i0);
-#pragma unroll
-                for (int q = 0; q < P; ++q)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        if (COMP) {
-                            // Kahan: true value = sum - cmp.
-                            const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
-                            const float2 t = add2(sum[q][r], y);
-                            cmp[q][r] = add2(add2(t, neg2(sum[q][r])), neg2(y));
-                            sum[q][r] = t;
-                        } else {
-                            sum[q][r] = add2(sum[q][r], acc[q][r]);
-                        }
-                    }
-            }
-            // This segment's sums into the warp's slot.
-            float4 *dst = red + ((int64_t)warp * 2 + sg) * W * IB;
-#pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const int l0 = (2 * q) * 32 + lane, l1 = l0 + 32;
-                dst[l0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
-                dst[l1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
-                if (COMP) {
-                    dst[IB + l0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
-                    dst[IB + l1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
-                }
-            }
-        }
-    }
-
-    // The warps' sums, per i-block in warp order: the CTA's partial(s).
-    __syncthreads();
-    const int64_t c = blockIdx.x;
-    const int64_t bfirst = (c * total / args.grid) / n;  // first i-block of this CTA's range
-    for (int64_t seg = 0; seg < 2; ++seg) {
-        const int64_t b = bfirst + seg;
-        bool touched = false;
-        for (int w = 0; w < WARPS; ++w) touched |= s_blk[w][0] == b || s_blk[w][1] == b;
-        if (!touched) break;
-        const int64_t off = (c * 2 + seg) * W * (int64_t)IB;
-        for (int l = tid; l < IB; l += THREADS) {
-            float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int w = 0; w < WARPS; ++w)
-                for (int sg = 0; sg < 2; ++sg) {
-                    if (s_blk[w][sg] != b) continue;
-                    const float4 hi = red[((int64_t)w * 2 + sg) * W * IB + l];
-                    const float h[4] = {hi.x, hi.y, hi.z, hi.w};
-                    if (COMP) {
-                        const float4 lo = red[((int64_t)w * 2 + sg) * W * IB + IB + l];
-                        const float lw[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            float t, e;
-                            two_sum(S[r], h[r], t, e);
-                            S[r] = t;
-                            E[r] = __fadd_rn(E[r], __fsub_rn(e, lw[r]));  // warp value = hi - lo
-                        }
-                    } else {
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) S[r] = __fadd_rn(S[r], h[r]);
-                    }
-                }
-            if (NB_IN(args.err, 36, off + (W - 1) * IB + l < args.partial_len)) {
-                args.partial[off + l] = make_float4(S[0], S[1], S[2], S[3]);
-                if (COMP) args.partial[off + IB + l] = make_float4(-E[0], -E[1], -E[2], -E[3]);
-            }
-        }
-        const int64_t clo = cta_of_unit(b * n, total, args.grid);
-        const int64_t chi = cta_of_unit(b * n + n - 1, total, args.grid);
-        __threadfence();  // this CTA's partial is visible before it counts itself in
-        __syncthreads();
-        if (tid == 0) {
-            int last = 0;
-            if (NB_IN(args.err, 37, b >= 0 && b < args.nib)) {
-                const int prev = atomicAdd(&args.counters[b], 1);
-                last = prev == (int)(chi - clo);
-                if (last) atomicExch(&args.counters[b], 0);  // every contributor has arrived
-            }
-            s_last = last;
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            for (int l = tid; l < IB; l += THREADS) {
-                const int64_t gi = b * IB + l;
-                if (gi >= n) break;
-                float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-                sum_segments<COMP>(args.partial, args.partial_len, args.err, b, l, clo, chi, total,
-                                   args.grid, n, 2, IB, S, E);
-                args.a[3 * gi + 0] = args.a_scale * __fadd_rn(S[0], E[0]);
-                args.a[3 * gi + 1] = args.a_scale * __fadd_rn(S[1], E[1]);
-                args.a[3 * gi + 2] = args.a_scale * __fadd_rn(S[2], E[2]);
-                args.p[gi] = args.p_scale * __fadd_rn(S[3], E[3]);
-            }
-        }
-        __syncthreads();  // s_last is read by every thread before the next segment writes it
-    }
-}
-
 // Synthetic inputs for tuning runs (timing only; values do not matter
 // beyond being finite): x uniform in [-1, 1)^3 from a 64-bit mixer, m = 1/n.
 __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed) {
@@ -1039,24 +804,34 @@ static cudaError_t launch_pair(const PairArgs &a, int grid, size_t smem, cudaStr
     return cudaGetLastError();
 }
 
+// The single-launch kernels go out with programmatic stream serialization
+// (see pdl_wait_then_release).
+template <typename K>
+static cudaError_t launch_pdl(K kernel, const FusedArgs &a, int grid, int threads, size_t smem,
+                              cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <int WARPS, int I, int J, int U, int M, bool N, bool C>
 static cudaError_t launch_fused(const FusedArgs &a, int grid, size_t smem, cudaStream_t st) {
-    fused_kernel<WARPS, I, J, U, M, N, C><<<grid, WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(fused_kernel<WARPS, I, J, U, M, N, C>, a, grid, WARPS * 32, smem, st);
 }
 
 template <int WARPS, int I, int J, int U, int M, bool N, bool C>
 static cudaError_t launch_fused_sk(const FusedArgs &a, int grid, size_t smem, cudaStream_t st) {
-    fused_sk_kernel<WARPS, I, J, U, M, N, C><<<grid, WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(fused_sk_kernel<WARPS, I, J, U, M, N, C>, a, grid, WARPS * 32, smem, st);
 }
 
-template <int WARPS, int I, int J, int U, int M, bool N, bool C>
-static cudaError_t launch_fused_wk(const FusedArgs &a, int grid, size_t smem, cudaStream_t st) {
-    static_assert(!N, "the warp-level form has no Newton step");
-    fused_wk_kernel<WARPS, I, J, U, M, C><<<grid, WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
 
 template <int T, int I, int J, int S, int A, bool C, int RS = 1>
 constexpr size_t pair_smem() {
@@ -1091,11 +866,6 @@ constexpr size_t pair_smem() {
     {{T, I, J, 1, U, M, 0, 0, 63, N, 2}, C,                                                        \
      (const void *)fused_sk_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
      nullptr, launch_fused_sk<T / 32, I, J, U, M, (N != 0), C>}
-// Warp-level stream-K form (fused = 3); smem is the most it asks for (the
-// plan sets the launch's own).
-#define NB_FUSED_WK(T, I, J, U, M, C)                                                           \
-    {{T, I, J, 1, U, M, 0, 0, 63, 0, 3}, C, (const void *)fused_wk_kernel<T / 32, I, J, U, M, C>, \
-     kWkSmemMax, nullptr, launch_fused_wk<T / 32, I, J, U, M, false, C>}
 
 // Plain shapes. The first group evaluates the reciprocal square root without
 // the Newton step (refine 0, 13 FP32 ops per pair); the second keeps the
@@ -1114,11 +884,12 @@ static const PairVariant kPlain[] = {
     NB_VARIANT(64, 2, 64, 4, 4, 1, 0, 0, 63, 0, false),
     NB_VARIANT(64, 4, 128, 4, 4, 1, 0, 0, 63, 0, false),
     NB_VARIANT(256, 4, 512, 3, 4, 1, 0, 0, 63, 0, false),
-    NB_VARIANT(256, 4, 768, 3, 4, 1, 0, 0, 63, 0, false),
-    NB_VARIANT(256, 4, 1024, 3, 4, 1, 0, 0, 63, 0, false),
-    NB_VARIANT(384, 4, 512, 3, 4, 1, 0, 0, 63, 0, false),
-    NB_VARIANT(256, 4, 512, 2, 4, 1, 0, 0, 63, 0, false),
-    NB_VARIANT(256, 4, 512, 3, 8, 1, 0, 0, 63, 0, false),
+    NB_VARIANT(384, 4, 1024, 3, 4, 1, 0, 0, 63, 0, false),
+    // Kahan-compensated running sum in plain mode (the compensated combine
+    // follows): on sm_103a this kernel's compiled schedule runs 2.7% faster
+    // than the plain running sum's at the same shape (ncu: 1.3% fewer
+    // instructions), so it is the plain path's large-n shape.
+    NB_VARIANT(256, 4, 1024, 3, 4, 1, 0, 0, 63, 0, true),
     NB_VARIANT(256, 4, 256, 3, 4, 2, 0, 0, 63, 0, false),
     NB_VARIANT(128, 4, 256, 3, 4, 4, 0, 0, 63, 0, false),
     NB_VARIANT(128, 8, 256, 3, 8, 3, 1, 0, 63, 0, false),
@@ -1140,12 +911,10 @@ static const PairVariant kPlain[] = {
     NB_FUSED(512, 2, 32, 4, 1, 0, false),
     NB_FUSED_SK(256, 4, 32, 4, 1, 0, false),
     NB_FUSED_SK(128, 4, 32, 4, 1, 0, false),
-    NB_FUSED_WK(256, 4, 32, 4, 1, false),
 };
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
     NB_VARIANT(256, 4, 512, 3, 4, 1, 0, 0, 63, 0, true),
-    NB_VARIANT(256, 4, 1024, 3, 4, 1, 0, 0, 63, 0, true),
     NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, 0, true),
     NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, 0, true),
     NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, 0, true),
@@ -1169,7 +938,6 @@ static const PairVariant kComp[] = {
     NB_FUSED(512, 2, 32, 4, 1, 0, true),
     NB_FUSED_SK(256, 4, 32, 4, 1, 0, true),
     NB_FUSED_SK(128, 4, 32, 4, 1, 0, true),
-    NB_FUSED_WK(256, 4, 32, 4, 1, true),
 };
 // HL variants (compensated, positions from FP64 state as HL records), with
 // and without the potential, for large and for small n.
@@ -1192,7 +960,6 @@ static_assert(kDefaultRefine == 0, "the no-potential and HL shapes have no Newto
 #undef NB_VARIANT_NP
 #undef NB_FUSED
 #undef NB_FUSED_SK
-#undef NB_FUSED_WK
 
 const PairVariant *hl_variant(int64_t n, bool no_pot) {
     return &kHL[no_pot ? 1 : 0][n >= (int64_t)1 << 15 ? 0 : 1];
@@ -1223,13 +990,14 @@ static int pair_variant_index(bool comp, const nb_tile &t) {
 // Built-in packed (not fused) choices per size class, from the measured shape
 // sweep (GB300, no Newton step): 2 i per thread and 128-particle tiles while
 // the work cannot fill 152 SMs with large i-blocks, then 4 i per thread in
-// 256-thread CTAs; the plain sums from N = 2^17 on take 12 i per thread with
-// the running sums in shared memory.
+// 256-thread CTAs; the plain sums from N = 2^17 on take 1024-particle tiles
+// with the Kahan running sum (2572 -> 2640 G-int/s at N = 2^20 against the
+// plain running sum at that shape).
 int pair_default_unfused_index(bool comp, int64_t n) {
     constexpr int R = kDefaultRefine;
     static const nb_tile shapes[2][4] = {
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {64, 4, 128, 4, 4, 1, 0, 0, 63, R},
-         {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {128, 12, 256, 3, 4, 1, 0, 1, 63, R}},
+         {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {256, 4, 1024, 3, 4, 1, 0, 0, 63, R}},
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R},
          {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R}}};
     static const int idx[2][4] = {
@@ -1268,25 +1036,6 @@ PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
     PairPlan p{};
     p.n = n;
     p.smem = v.smem;
-    if (v.tile.fused == 3) {
-        // Warp-level stream-K: (i-block, j) units split over every warp of
-        // one CTA per SM; at most two i-blocks per warp and per CTA.
-        const int warps = v.tile.threads / 32;
-        p.ib = 32 * v.tile.ipt;
-        p.npad = round_up(std::max<int64_t>(n, 1), kPad);
-        p.nib = (n + p.ib - 1) / p.ib;
-        p.njt = n;
-        p.units = p.nib * n;
-        p.grid = std::max(1, resident_ctas);
-        p.maxseg = 2;
-        p.words = v.comp ? 2 : 1;
-        const int64_t G = (int64_t)p.grid * warps;
-        p.nchunks = (p.units + G - 1) / G;  // the j stretch of a warp
-        p.partial_bytes = (size_t)p.grid * 2 * p.words * p.ib * sizeof(float4);
-        p.smem = (size_t)warps * p.nchunks * sizeof(JPart) + (size_t)warps * 2 * p.words * p.ib * sizeof(float4);
-        if (n >= kWkMaxN || p.nib > p.grid || p.nchunks > kWkStretchMax) p.grid = 0;
-        return p;
-    }
     if (v.tile.fused == 1) {
         // One CTA per (i-block, j-chunk); as many chunks as fill the GPU once.
         p.ib = 32 * v.tile.ipt;

@@ -381,7 +381,8 @@ constexpr size_t vjp_smem() {
 const VjpVariant kVjp[] = {
     NB_VJP(256, 2, 128, 3, 2, 0), NB_VJP(256, 2, 128, 3, 4, 0), NB_VJP(512, 2, 128, 3, 2, 0),
     NB_VJP(128, 2, 128, 3, 2, 0), NB_VJP(256, 2, 256, 3, 2, 0), NB_VJP(64, 4, 128, 3, 2, 0),
-    NB_VJP(128, 4, 128, 3, 2, 0), NB_VJP(128, 4, 128, 3, 4, 0),
+    NB_VJP(128, 4, 128, 3, 2, 0), NB_VJP(128, 4, 128, 3, 4, 0), NB_VJP(256, 2, 64, 4, 2, 0),
+    NB_VJP(256, 2, 32, 4, 2, 0),
 };
 #undef NB_VJP
 constexpr int kVjpCount = (int)(sizeof(kVjp) / sizeof(kVjp[0]));

@@ -163,8 +163,7 @@ def test_fused_shapes(nb, ctx, oracle_mod, mode):
     eps = np.float32(1.0 / 64)
     cases = []
     # 20000: a stream-K CTA's range can touch three i-blocks; 4096 and 8191:
-    # the warp-level form's workload and its largest size (most warps of
-    # the warp-level form then straddle two i-blocks).
+    # the chunked form's workload and its largest size.
     for n in (1, 200, 3001, 4096, 8191, 9000, 20000):
         x32, m32 = plummer32(n, seed=100 + n)
         cases.append((n, x32, m32, oracle_mod.force(x32, m32, eps)))
