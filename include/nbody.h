@@ -114,7 +114,16 @@ typedef struct nb_ctx nb_ctx;
  * is the same kernel with the pair kernel's work split: the (i-block,
  * `jtile`-particle tile) units are divided into equal contiguous ranges,
  * one per resident CTA, so a CTA may finish one i-block and start the next;
- * the last contributing CTA adds the partials in CTA order. Callers that
+ * the last contributing CTA adds the partials in CTA order. `fused` = 3 is
+ * the chunked split with the chunks of an i-block launched as one
+ * thread-block cluster (at most 8 chunks): the chunk partials stay in each
+ * CTA's shared memory and CTA r of the cluster adds, in chunk order, those of
+ * every nch-th particle through distributed shared memory (no partials in
+ * global memory, no arrival counts); when the GPU cannot hold all of its
+ * clusters at once, the call runs the chunked form of the same shape. All
+ * single-launch shapes are launched with programmatic stream serialization:
+ * the next kernel on the stream may be scheduled while the previous one runs,
+ * and each waits for its predecessor's results before reading. Callers that
  * pass packed FP64 state (the leap-frog) use the non-fused shape of the same
  * size class instead. */
 typedef struct nb_tile {
@@ -294,12 +303,13 @@ nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, f
                        const float *ga, const float *gp, float *gx, float *gm, void *stream);
 
 /* Shape of nb_force_vjp's pair kernel (nb_tile fields threads, ipt, jtile,
- * stages, unroll, sums_in_smem; the others as listed): force one of the
- * compiled shapes listed by nb_list_vjp_tiles (NULL restores the built-in
- * choice), read the shape in use, list the compiled shapes (up to `cap`
- * written to out, which may be NULL; the total in *count). */
+ * stages, unroll, minblocks, sums_in_smem; the others as listed): force one
+ * of the compiled shapes listed by nb_list_vjp_tiles (NULL restores the
+ * built-in choice by size), read the shape nb_force_vjp uses at size n, list
+ * the compiled shapes (up to `cap` written to out, which may be NULL; the
+ * total in *count). */
 nb_status nb_set_vjp_tile(nb_ctx *ctx, const nb_tile *tile);
-nb_status nb_get_vjp_tile(nb_ctx *ctx, nb_tile *out);
+nb_status nb_get_vjp_tile(nb_ctx *ctx, int64_t n, nb_tile *out);
 nb_status nb_list_vjp_tiles(nb_tile *out, int cap, int *count);
 
 /*

@@ -96,7 +96,7 @@ _SIGNATURES = {
     "nb_energy": (_c.c_int, [_P, _P, _P, _P, _I64, _c.c_float, _P, _c.c_int, _P]),
     "nb_force_vjp": (_c.c_int, [_P, _P, _P, _I64, _c.c_float, _P, _P, _P, _P, _P]),
     "nb_set_vjp_tile": (_c.c_int, [_P, _c.POINTER(nb_tile)]),
-    "nb_get_vjp_tile": (_c.c_int, [_P, _c.POINTER(nb_tile)]),
+    "nb_get_vjp_tile": (_c.c_int, [_P, _I64, _c.POINTER(nb_tile)]),
     "nb_list_vjp_tiles": (_c.c_int, [_c.POINTER(nb_tile), _c.c_int, _c.POINTER(_c.c_int)]),
     "nb_synchronize": (_c.c_int, [_P, _P]),
     "nb_get_tile": (_c.c_int, [_P, _I64, _c.c_int, _c.POINTER(nb_tile)]),
@@ -414,9 +414,9 @@ def nb_set_vjp_tile(ctx, tile) -> None:
     _check(ctx, library().nb_set_vjp_tile(ctx.handle, ctypes.byref(tile)))
 
 
-def nb_get_vjp_tile(ctx) -> nb_tile:
+def nb_get_vjp_tile(ctx, n=1 << 20) -> nb_tile:
     t = nb_tile()
-    _check(ctx, library().nb_get_vjp_tile(ctx.handle, ctypes.byref(t)))
+    _check(ctx, library().nb_get_vjp_tile(ctx.handle, int(n), ctypes.byref(t)))
     return t
 
 

@@ -53,6 +53,7 @@ struct nb_ctx {
     int override_idx[2] = {0, 0};
     std::map<int, int> tuned[2];           // size class -> variant index
     std::map<const void *, int> occupancy;  // kernel -> resident CTAs per SM
+    std::map<std::pair<const void *, int>, int> clusters;  // (kernel, size) -> co-resident clusters
 
     // timing
     bool timing = false;
@@ -188,6 +189,30 @@ int resident_ctas(nb_ctx *ctx, const PairVariant &v) {
     return per_sm * ctx->sm_count;
 }
 
+// Clusters of `size` CTAs of v's kernel that the GPU holds at once (the
+// cluster form needs all of its clusters resident in one wave to pay off).
+int max_active_clusters(nb_ctx *ctx, const PairVariant &v, int size) {
+    const auto key = std::make_pair(v.kernel, size);
+    auto it = ctx->clusters.find(key);
+    if (it != ctx->clusters.end()) return it->second;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(size * ctx->sm_count));
+    cfg.blockDim = dim3((unsigned)v.tile.threads);
+    cfg.dynamicSmemBytes = v.smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, v.kernel, &cfg) != cudaSuccess) num = 0;
+    cudaGetLastError();
+    ctx->clusters[key] = num;
+    return num;
+}
+
 const PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp) {
     const int m = comp ? 1 : 0;
     if (ctx->has_override[m]) return *pair_variant(comp, ctx->override_idx[m]);
@@ -208,6 +233,13 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     // No potential wanted: the same shape without the potential term, if compiled.
     if (!p)
         if (const PairVariant *tw = no_pot_twin(*vp)) vp = tw;
+    // The cluster form when its clusters do not all fit at once: the chunked
+    // form of the same shape (same split, partials through global memory).
+    if (vp->tile.fused == 3) {
+        const PairPlan cp = make_plan(*vp, n, resident_ctas(ctx, *vp));
+        if (max_active_clusters(ctx, *vp, (int)cp.nchunks) < cp.nib)
+            if (const PairVariant *tw = chunked_twin(*vp)) vp = tw;
+    }
     const PairVariant &v = *vp;
     const PairPlan plan = make_plan(v, n, resident_ctas(ctx, v));
     cudaError_t e;

@@ -145,6 +145,8 @@ const PairVariant *hl_variant(int64_t n, bool no_pot = false);
 // The twin of a plain packed shape that sums a_i only (12 FP32 operations
 // per pair), or nullptr if that shape has none.
 const PairVariant *no_pot_twin(const PairVariant &v);
+// The chunked form (fused = 1) of a single-launch shape, or nullptr.
+const PairVariant *chunked_twin(const PairVariant &v);
 int pair_variant_count(bool comp);
 const PairVariant *pair_variant(bool comp, int idx);
 int pair_default_index(bool comp, int64_t n);

@@ -35,6 +35,7 @@
 //    and the FP32 Newton step does not improve on it, so the built-in
 //    shapes omit it.
 #include <algorithm>
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "nb_combine.cuh"
@@ -414,6 +415,7 @@ __global__ void reduce_kernel(const ReduceArgs r) {
 // Every addition order is fixed by the launch shape, so results are
 // bit-reproducible; there are no waits on other CTAs.
 constexpr int kFusedJmax = 1024;  // particles per shared-memory block (32 KB)
+constexpr int kMaxClusterChunks = 8;  // portable thread-block cluster size
 
 // Load particles j0 .. j0 + cnt - 1 (cnt <= kFusedJmax) from x, m and pack
 // them into blk; rows at or beyond n are inert (m = 0 at the origin). Each
@@ -780,6 +782,179 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster form of the chunked fused kernel (tile field fused = 3). The same
+// work split as fused_kernel -- one CTA per (i-block, j-chunk), all warps on
+// the same i, the chunk's tiles shared among the warps -- but the nch CTAs of
+// an i-block form one thread-block cluster, and the chunks' partial sums meet
+// in distributed shared memory: each CTA leaves its partial in its own shared
+// memory, the cluster synchronises, and CTA r of the cluster adds the nch
+// partials of the i-particles l = r, r + nch, ... in chunk order (the chunked
+// form's order and arithmetic, so the results are the same bits) and writes
+// a_i, p_i. No partials in global memory, no fence, no arrival count; a
+// second cluster barrier keeps every CTA's shared memory alive until the
+// others have read it. Launched with the cluster size nch (<= 8) as a launch
+// attribute.
+template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
+__global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedArgs args) {
+    namespace cg = cooperative_groups;
+    static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");
+    static_assert(kFusedJmax % JT == 0, "blocks hold whole tiles");
+    constexpr int THREADS = WARPS * 32;
+    constexpr int P = IPT / 2;
+    constexpr int IB = 32 * IPT;
+    constexpr int W = COMP ? 2 : 1;  // float4 words per i in a partial
+    constexpr int TPB = kFusedJmax / JT;
+    static_assert(kPad % IB == 0, "i-blocks must divide the padding");
+    static_assert(WARPS * W * IB * sizeof(float4) <= kFusedJmax * sizeof(JPart),
+                  "the cross-warp sums reuse the particle block");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    JPart *blk = reinterpret_cast<JPart *>(smem);
+    float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after the last block
+    float4 *cpart = reinterpret_cast<float4 *>(smem + kFusedJmax * sizeof(JPart));  // [W][IB]
+    pdl_wait_then_release();
+    cg::cluster_group cluster = cg::this_cluster();
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = args.n, nch = args.nchunks;
+    const int64_t b = blockIdx.x / nch;
+    const int c = (int)cluster.block_rank();  // = blockIdx.x % nch
+    const int64_t t0 = c * args.njt / nch, t1 = (c + 1) * args.njt / nch;  // chunk's tiles
+
+    float2 xi[P], yi[P], zi[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int64_t i0 = b * IB + (2 * q) * 32 + lane, i1 = i0 + 32;
+        float3 p0 = make_float3(0.f, 0.f, 0.f), p1 = p0;
+        if (i0 < n) p0 = make_float3(args.x[3 * i0], args.x[3 * i0 + 1], args.x[3 * i0 + 2]);
+        if (i1 < n) p1 = make_float3(args.x[3 * i1], args.x[3 * i1 + 1], args.x[3 * i1 + 2]);
+        xi[q] = make_float2(p0.x, p1.x);
+        yi[q] = make_float2(p0.y, p1.y);
+        zi[q] = make_float2(p0.z, p1.z);
+    }
+    const float2 eps2 = splat2(args.eps2);
+    const float2 zero2 = splat2(0.f);
+    float2 sum[P][4], cmp[P][4];
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) sum[q][r] = cmp[q][r] = zero2;
+
+    for (int64_t bt0 = t0; bt0 < t1; bt0 += TPB) {
+        const int64_t bt1 = bt0 + TPB < t1 ? bt0 + TPB : t1;
+        const int cnt = (int)(bt1 - bt0) * JT;
+        pack_block<THREADS>(args.x, args.m, n, bt0 * JT, cnt, blk);
+        __syncthreads();
+        for (int64_t t = bt0 + warp; t < bt1; t += WARPS) {
+            const JPart *T = blk + (t - bt0) * JT;
+            float2 acc[P][4];
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[q][r] = zero2;
+            const int64_t ibase = b * IB, jbase = t * JT;
+            int self0[P], self1[P];
+            if (jbase < ibase + IB && ibase < jbase + JT) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
+                    self1[q] = self0[q] + 32;
+                }
+                tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+            } else {
+                tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (COMP) {
+                        // Kahan: true value = sum - cmp.
+                        const float2 y = add2(acc[q][r], neg2(cmp[q][r]));
+                        const float2 tt = add2(sum[q][r], y);
+                        cmp[q][r] = add2(add2(tt, neg2(sum[q][r])), neg2(y));
+                        sum[q][r] = tt;
+                    } else {
+                        sum[q][r] = add2(sum[q][r], acc[q][r]);
+                    }
+                }
+        }
+        __syncthreads();  // the block is read by every warp before it is refilled
+    }
+
+    // The warps' sums, added in warp order: this CTA's partial, kept in its
+    // own shared memory for the cluster.
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int i0 = (2 * q) * 32 + lane, i1 = i0 + 32;
+        float4 *dst = red + (int64_t)warp * W * IB;
+        dst[i0] = make_float4(sum[q][0].x, sum[q][1].x, sum[q][2].x, sum[q][3].x);
+        dst[i1] = make_float4(sum[q][0].y, sum[q][1].y, sum[q][2].y, sum[q][3].y);
+        if (COMP) {
+            dst[IB + i0] = make_float4(cmp[q][0].x, cmp[q][1].x, cmp[q][2].x, cmp[q][3].x);
+            dst[IB + i1] = make_float4(cmp[q][0].y, cmp[q][1].y, cmp[q][2].y, cmp[q][3].y);
+        }
+    }
+    __syncthreads();
+    for (int l = tid; l < IB; l += THREADS) {
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int w = 0; w < WARPS; ++w) {
+            const float4 hi = red[(int64_t)w * W * IB + l];
+            const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+            if (COMP) {
+                const float4 lo = red[(int64_t)w * W * IB + IB + l];
+                const float lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float t, e;
+                    two_sum(S[r], h[r], t, e);
+                    S[r] = t;
+                    E[r] = __fadd_rn(E[r], __fsub_rn(e, lw[r]));  // warp value = hi - lo
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) S[r] = __fadd_rn(S[r], h[r]);
+            }
+        }
+        cpart[l] = make_float4(S[0], S[1], S[2], S[3]);
+        if (COMP) cpart[IB + l] = make_float4(-E[0], -E[1], -E[2], -E[3]);
+    }
+    cluster.sync();  // every chunk's partial is in its CTA's shared memory
+
+    // CTA c adds, for i-particles l = c, c + nch, ..., the nch partials in
+    // chunk order (the chunked form's combine) and writes a_i, p_i.
+    for (int l = c + tid * (int)nch; l < IB; l += THREADS * (int)nch) {
+        const int64_t gi = b * IB + l;
+        if (gi >= n) break;
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < (int)nch; ++k) {
+            const float4 *src = cluster.map_shared_rank(cpart, k);
+            const float4 hi = src[l];
+            const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+            if (COMP) {
+                const float4 lo = src[IB + l];
+                const float lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float t, e;
+                    two_sum(S[r], h[r], t, e);
+                    S[r] = t;
+                    E[r] = __fadd_rn(E[r], __fsub_rn(e, lw[r]));  // chunk value = hi - lo
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) S[r] = __fadd_rn(S[r], h[r]);
+            }
+        }
+        args.a[3 * gi + 0] = args.a_scale * __fadd_rn(S[0], E[0]);
+        args.a[3 * gi + 1] = args.a_scale * __fadd_rn(S[1], E[1]);
+        args.a[3 * gi + 2] = args.a_scale * __fadd_rn(S[2], E[2]);
+        args.p[gi] = args.p_scale * __fadd_rn(S[3], E[3]);
+    }
+    cluster.sync();  // the other CTAs have read this CTA's partial
+}
+
 // Synthetic inputs for tuning runs (timing only; values do not matter
 // beyond being finite): x uniform in [-1, 1)^3 from a 64-bit mixer, m = 1/n.
 __global__ void fill_uniform_kernel(float *x, float *m, int64_t n, uint64_t seed) {
@@ -832,6 +1007,27 @@ static cudaError_t launch_fused_sk(const FusedArgs &a, int grid, size_t smem, cu
     return launch_pdl(fused_sk_kernel<WARPS, I, J, U, M, N, C>, a, grid, WARPS * 32, smem, st);
 }
 
+// The cluster form: clusters of a.nchunks CTAs (one i-block each), plus the
+// programmatic dependent launch of the other single-launch kernels.
+template <int WARPS, int I, int J, int U, int M, bool N, bool C>
+static cudaError_t launch_fused_cl(const FusedArgs &a, int grid, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)(WARPS * 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = (unsigned)a.nchunks;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, fused_cl_kernel<WARPS, I, J, U, M, N, C>, a);
+}
+
 
 template <int T, int I, int J, int S, int A, bool C, int RS = 1>
 constexpr size_t pair_smem() {
@@ -861,6 +1057,13 @@ constexpr size_t pair_smem() {
     {{T, I, J, 1, U, M, 0, 0, 63, N, 1}, C,                                                     \
      (const void *)fused_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
      nullptr, launch_fused<T / 32, I, J, U, M, (N != 0), C>}
+// The chunked shapes in cluster form (fused = 3): the particle block plus
+// one CTA partial in shared memory.
+#define NB_FUSED_CL(T, I, J, U, M, N, C)                                                          \
+    {{T, I, J, 1, U, M, 0, 0, 63, N, 3}, C,                                                        \
+     (const void *)fused_cl_kernel<T / 32, I, J, U, M, (N != 0), C>,                               \
+     kFusedJmax * sizeof(JPart) + (C ? 2 : 1) * 32 * I * sizeof(float4), nullptr,                  \
+     launch_fused_cl<T / 32, I, J, U, M, (N != 0), C>}
 // The same shapes in stream-K form (fused = 2).
 #define NB_FUSED_SK(T, I, J, U, M, N, C)                                                        \
     {{T, I, J, 1, U, M, 0, 0, 63, N, 2}, C,                                                        \
@@ -911,6 +1114,8 @@ static const PairVariant kPlain[] = {
     NB_FUSED(512, 2, 32, 4, 1, 0, false),
     NB_FUSED_SK(256, 4, 32, 4, 1, 0, false),
     NB_FUSED_SK(128, 4, 32, 4, 1, 0, false),
+    NB_FUSED_CL(256, 4, 32, 4, 1, 0, false),
+    NB_FUSED_CL(256, 2, 32, 4, 1, 0, false),
 };
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
@@ -938,6 +1143,8 @@ static const PairVariant kComp[] = {
     NB_FUSED(512, 2, 32, 4, 1, 0, true),
     NB_FUSED_SK(256, 4, 32, 4, 1, 0, true),
     NB_FUSED_SK(128, 4, 32, 4, 1, 0, true),
+    NB_FUSED_CL(256, 4, 32, 4, 1, 0, true),
+    NB_FUSED_CL(256, 2, 32, 4, 1, 0, true),
 };
 // HL variants (compensated, positions from FP64 state as HL records), with
 // and without the potential, for large and for small n.
@@ -960,9 +1167,19 @@ static_assert(kDefaultRefine == 0, "the no-potential and HL shapes have no Newto
 #undef NB_VARIANT_NP
 #undef NB_FUSED
 #undef NB_FUSED_SK
+#undef NB_FUSED_CL
+
+static int pair_variant_index(bool comp, const nb_tile &t);
 
 const PairVariant *hl_variant(int64_t n, bool no_pot) {
     return &kHL[no_pot ? 1 : 0][n >= (int64_t)1 << 15 ? 0 : 1];
+}
+
+const PairVariant *chunked_twin(const PairVariant &v) {
+    nb_tile t = v.tile;
+    t.fused = 1;
+    const int k = pair_variant_index(v.comp, t);
+    return k >= 0 ? pair_variant(v.comp, k) : nullptr;
 }
 
 const PairVariant *no_pot_twin(const PairVariant &v) {
@@ -1011,12 +1228,14 @@ int pair_default_unfused_index(bool comp, int64_t n) {
 }
 
 // Single-launch shapes by size (GB300, whole calls, plain / compensated):
-// the chunked form below kChunkedMaxN (N = 4096: 14.4 us against 30.7 us for
-// pack + pair + combine), the stream-K form from there to kFusedMaxN (N =
-// 12288: 76.6 / 80.0 us against 92.2 / 94.4 us for the best packed shapes;
+// the cluster form below kChunkedMaxN (N = 4096: 11.9 / 12.1 us against
+// 12.6 / 13.3 for the chunked form and 30.7 for pack + pair + combine; N =
+// 2048: 6.0 against 7.0), the stream-K form from there to kFusedMaxN (N =
+// 12288: 73.8 / 77.5 us against 92.2 / 94.4 us for the best packed shapes;
 // N = 16384: 129.0 / 133.5 against 137.2 / 141.3 us), the packed shapes
 // above (N = 24576: stream-K 279.0 / 290.5 us against 280.5 / 280.7).
 constexpr int64_t kChunkedMaxN = (int64_t)1 << 13;
+constexpr int64_t kClusterWideMinN = (int64_t)1 << 12;
 constexpr int64_t kFusedMaxN = (int64_t)3 << 13;
 
 bool fused_candidate(int64_t n) { return n < (int64_t)1 << 16; }
@@ -1024,11 +1243,17 @@ bool fused_candidate(int64_t n) { return n < (int64_t)1 << 16; }
 int pair_default_index(bool comp, int64_t n) {
     if (n >= kFusedMaxN) return pair_default_unfused_index(comp, n);
     constexpr int R = kDefaultRefine;
-    static const nb_tile chunked{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 1};
+    // Below kChunkedMaxN the cluster form (the chunked split, partials met in
+    // distributed shared memory; it runs as the chunked form when its
+    // clusters do not fit at once): 2 i per lane below 4096, 4 from there.
+    static const nb_tile cl2{256, 2, 32, 1, 4, 1, 0, 0, 63, R, 3};
+    static const nb_tile cl4{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 3};
     static const nb_tile streamk{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 2};
-    static const int idx[2][2] = {{pair_variant_index(false, chunked), pair_variant_index(true, chunked)},
+    static const int idx[3][2] = {{pair_variant_index(false, cl2), pair_variant_index(true, cl2)},
+                                  {pair_variant_index(false, cl4), pair_variant_index(true, cl4)},
                                   {pair_variant_index(false, streamk), pair_variant_index(true, streamk)}};
-    const int k = idx[n < kChunkedMaxN ? 0 : 1][comp ? 1 : 0];
+    const int cls = n < kClusterWideMinN ? 0 : n < kChunkedMaxN ? 1 : 2;
+    const int k = idx[cls][comp ? 1 : 0];
     return k >= 0 ? k : pair_default_unfused_index(comp, n);
 }
 
@@ -1036,6 +1261,23 @@ PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
     PairPlan p{};
     p.n = n;
     p.smem = v.smem;
+    if (v.tile.fused == 3) {
+        // Cluster form: one CTA per (i-block, j-chunk), the chunks of an
+        // i-block one cluster of at most kMaxClusterChunks CTAs; no global
+        // partials.
+        p.ib = 32 * v.tile.ipt;
+        p.npad = round_up(std::max<int64_t>(n, 1), kPad);
+        p.nib = (n + p.ib - 1) / p.ib;
+        p.njt = (n + v.tile.jtile - 1) / v.tile.jtile;
+        p.nchunks = std::max<int64_t>(
+            1, std::min<int64_t>({p.njt, (int64_t)kMaxClusterChunks, resident_ctas / std::max<int64_t>(p.nib, 1)}));
+        p.units = p.nib * p.nchunks;
+        p.grid = (int)p.units;
+        p.maxseg = 1;
+        p.words = v.comp ? 2 : 1;
+        p.partial_bytes = 0;
+        return p;
+    }
     if (v.tile.fused == 1) {
         // One CTA per (i-block, j-chunk); as many chunks as fill the GPU once.
         p.ib = 32 * v.tile.ipt;

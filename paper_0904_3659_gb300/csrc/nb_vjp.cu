@@ -145,8 +145,8 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
 // stages), UNR (unroll of the j loop), ACCS (running sums in shared memory,
 // one slot per thread, touched once per tile: frees 16 registers per pair).
 // GP: the upstream gradient on p is not zero (its terms are summed).
-template <int THREADS, int IPT, int JT, int STAGES, int UNR, int ACCS, bool GP>
-__global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs args) {
+template <int THREADS, int IPT, int JT, int STAGES, int UNR, int ACCS, bool GP, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, MINB) vjp_kernel(const VjpArgs args) {
     constexpr int P = IPT / 2;
     constexpr int IB = THREADS * IPT;
     constexpr uint32_t TILE_BYTES = JT * sizeof(VPart);
@@ -362,9 +362,9 @@ struct VjpVariant {
     void (*launch[2])(const VjpArgs &, int grid, size_t smem, cudaStream_t);
 };
 
-template <int T, int I, int J, int S, int U, int A, bool G>
+template <int T, int I, int J, int S, int U, int A, bool G, int M>
 void launch_vjp(const VjpArgs &a, int grid, size_t smem, cudaStream_t st) {
-    vjp_kernel<T, I, J, S, U, A, G><<<grid, T, smem, st>>>(a);
+    vjp_kernel<T, I, J, S, U, A, G, M><<<grid, T, smem, st>>>(a);
 }
 
 template <int T, int I, int J, int S, int A>
@@ -373,11 +373,13 @@ constexpr size_t vjp_smem() {
            (size_t)S * sizeof(uint64_t);
 }
 
-#define NB_VJP(T, I, J, S, U, A)                                                             \
-    {{T, I, J, S, U, 1, 0, A, 63, kDefaultRefine, 0},                                        \
-     {(const void *)vjp_kernel<T, I, J, S, U, A, false>,                                    \
-      (const void *)vjp_kernel<T, I, J, S, U, A, true>},                                    \
-     vjp_smem<T, I, J, S, A>(), {launch_vjp<T, I, J, S, U, A, false>, launch_vjp<T, I, J, S, U, A, true>}}
+#define NB_VJP_M(T, I, J, S, U, A, M)                                                        \
+    {{T, I, J, S, U, M, 0, A, 63, kDefaultRefine, 0},                                        \
+     {(const void *)vjp_kernel<T, I, J, S, U, A, false, M>,                                 \
+      (const void *)vjp_kernel<T, I, J, S, U, A, true, M>},                                 \
+     vjp_smem<T, I, J, S, A>(),                                                             \
+     {launch_vjp<T, I, J, S, U, A, false, M>, launch_vjp<T, I, J, S, U, A, true, M>}}
+#define NB_VJP(T, I, J, S, U, A) NB_VJP_M(T, I, J, S, U, A, 1)
 const VjpVariant kVjp[] = {
     NB_VJP(256, 2, 128, 3, 2, 0), NB_VJP(256, 2, 128, 3, 4, 0), NB_VJP(512, 2, 128, 3, 2, 0),
     NB_VJP(128, 2, 128, 3, 2, 0), NB_VJP(256, 2, 256, 3, 2, 0), NB_VJP(64, 4, 128, 3, 2, 0),
@@ -385,12 +387,19 @@ const VjpVariant kVjp[] = {
     NB_VJP(256, 2, 32, 4, 2, 0),
 };
 #undef NB_VJP
+#undef NB_VJP_M
 constexpr int kVjpCount = (int)(sizeof(kVjp) / sizeof(kVjp[0]));
-constexpr int kVjpDefault = 0;
+// Built-in shapes by size (GB300 sweep, G-pairs/s): 64-particle j-tiles below
+// 2^15 (N = 16384: 936 against 912 for 128-particle tiles; the finer
+// (i-block, j-tile) units balance the persistent split), 256-particle tiles
+// from there (N = 65536: 1015 against 982). Shapes that force more resident
+// warps per SM (minblocks 3 or 6) spilled and ran 8-11% slower.
+constexpr int kVjpSmall = 8, kVjpLarge = 4;
 
-const VjpVariant &vjp_variant(nb_ctx *ctx) {
+const VjpVariant &vjp_variant(nb_ctx *ctx, int64_t n) {
     const int k = ctx_ext(ctx).vjp_idx;
-    return kVjp[k >= 0 && k < kVjpCount ? k : kVjpDefault];
+    if (k >= 0 && k < kVjpCount) return kVjp[k];
+    return kVjp[n < ((int64_t)1 << 15) ? kVjpSmall : kVjpLarge];
 }
 
 }  // namespace
@@ -406,7 +415,7 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
     DeviceGuard g(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    const VjpVariant &vv = vjp_variant(ctx);
+    const VjpVariant &vv = vjp_variant(ctx, n);
     const int with_gp = gp ? 1 : 0;
     PairVariant shape{};
     shape.tile = vv.tile;
@@ -465,9 +474,9 @@ extern "C" nb_status nb_set_vjp_tile(nb_ctx *ctx, const nb_tile *tile) {
     return fail(ctx, NB_ERR_ARG, "tile shape is not one of the compiled VJP shapes");
 }
 
-extern "C" nb_status nb_get_vjp_tile(nb_ctx *ctx, nb_tile *out) {
+extern "C" nb_status nb_get_vjp_tile(nb_ctx *ctx, int64_t n, nb_tile *out) {
     if (!ctx || !out) return NB_ERR_ARG;
-    *out = vjp_variant(ctx).tile;
+    *out = vjp_variant(ctx, n).tile;
     return NB_OK;
 }
 

@@ -51,13 +51,13 @@ def test_host_only_calls(lib):
         assert t.stages >= (1 if t.fused else 2)
         assert t.threads % 32 == 0 and t.release in (0, 1) and t.unroll >= 1
         assert (t.jtile * 32) % 16 == 0
-        assert t.refine in (0, 1) and t.fused in (0, 1, 2)
+        assert t.refine in (0, 1) and t.fused in (0, 1, 2, 3)
     # Both arithmetic forms are compiled in each mode: the special-function
     # unit's rsqrt as is (the built-in default) and with one Newton step.
     for mode in (lib.NB_PLAIN, lib.NB_COMPENSATED):
         assert {t.refine for t in lib.nb_list_tiles(mode)} == {0, 1}
-        # Both single-launch forms: chunked (1) and stream-K (2).
-        assert {t.fused for t in lib.nb_list_tiles(mode)} == {0, 1, 2}
+        # The single-launch forms: chunked (1), stream-K (2), cluster (3).
+        assert {t.fused for t in lib.nb_list_tiles(mode)} == {0, 1, 2, 3}
     # The adjoint kernel's shapes: packed pairs, tiles dividing the padding.
     vjp = lib.nb_list_vjp_tiles()
     assert len(vjp) >= 2

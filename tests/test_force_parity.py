@@ -117,12 +117,12 @@ def test_default_shapes_skip_newton_step(nb, ctx):
 
 
 def test_default_path_by_size(nb):
-    # Built-in choice without tuning: the chunked single-launch shape below
-    # 8192, its stream-K form up to 24576, pack -> pair -> combine above.
+    # Built-in choice without tuning: the cluster single-launch shape below
+    # 8192, the stream-K form up to 24576, pack -> pair -> combine above.
     fresh = nb.Context(0)
     try:
         for mode in (0, 1):
-            for n, fused in ((1, 1), (4096, 1), (8191, 1), (8192, 2), (16384, 2), (24575, 2),
+            for n, fused in ((1, 3), (4096, 3), (8191, 3), (8192, 2), (16384, 2), (24575, 2),
                              (24576, 0), (1 << 20, 0)):
                 assert nb.nb_get_tile(fresh, n, mode).fused == fused, (mode, n)
     finally:
@@ -162,8 +162,9 @@ def test_fused_shapes(nb, ctx, oracle_mod, mode):
     assert fused
     eps = np.float32(1.0 / 64)
     cases = []
-    # 20000: a stream-K CTA's range can touch three i-blocks; 4096 and 8191:
-    # the chunked form's workload and its largest size.
+    # 20000: a stream-K CTA's range can touch three i-blocks (and the cluster
+    # form falls to one CTA per cluster); 4096 and 8191: the chunked and
+    # cluster forms' workload and their largest built-in size.
     for n in (1, 200, 3001, 4096, 8191, 9000, 20000):
         x32, m32 = plummer32(n, seed=100 + n)
         cases.append((n, x32, m32, oracle_mod.force(x32, m32, eps)))

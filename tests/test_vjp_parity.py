@@ -124,7 +124,7 @@ def test_every_vjp_shape(nb, ctx, oracle_mod):
     try:
         for t in tiles:
             nb.nb_set_vjp_tile(ctx, t)
-            assert nb.nb_get_vjp_tile(ctx).as_tuple() == t.as_tuple()
+            assert nb.nb_get_vjp_tile(ctx, n).as_tuple() == t.as_tuple()
             gx, gm = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
             gx2, gm2 = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
             assert gx.tobytes() == gx2.tobytes() and gm.tobytes() == gm2.tobytes(), t
