@@ -234,7 +234,10 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
     if (!p)
         if (const PairVariant *tw = no_pot_twin(*vp)) vp = tw;
     // The cluster form when its clusters do not all fit at once: the chunked
-    // form of the same shape (same split, partials through global memory).
+    // form of the same shape and split (partials through global memory).
+    // Smaller clusters that fit would mean longer chunks: at N = 6144 the
+    // 4-wide shape's clusters of 3 do not all fit, and clusters of 2 ran
+    // 28.2 us against 21.0 for the chunked form.
     if (vp->tile.fused == 3) {
         const PairPlan cp = make_plan(*vp, n, resident_ctas(ctx, *vp));
         if (max_active_clusters(ctx, *vp, (int)cp.nchunks) < cp.nib)

@@ -415,7 +415,12 @@ __global__ void reduce_kernel(const ReduceArgs r) {
 // Every addition order is fixed by the launch shape, so results are
 // bit-reproducible; there are no waits on other CTAs.
 constexpr int kFusedJmax = 1024;  // particles per shared-memory block (32 KB)
-constexpr int kMaxClusterChunks = 8;  // portable thread-block cluster size
+// Largest cluster of the cluster form: the portable 8 CTAs (clusters of up
+// to 16 measured no faster at N = 4096).
+constexpr int kMaxClusterChunks = 8;
+// Received partials per CTA of a cluster: ceil(IB / nch) slots x nch chunks,
+// at most IB + nch - 1, for the largest i-block of the cluster shapes.
+constexpr int kClusterSlots = 128 + kMaxClusterChunks;
 
 // Load particles j0 .. j0 + cnt - 1 (cnt <= kFusedJmax) from x, m and pack
 // them into blk; rows at or beyond n are inert (m = 0 at the origin). Each
@@ -787,13 +792,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
 // work split as fused_kernel -- one CTA per (i-block, j-chunk), all warps on
 // the same i, the chunk's tiles shared among the warps -- but the nch CTAs of
 // an i-block form one thread-block cluster, and the chunks' partial sums meet
-// in distributed shared memory: each CTA leaves its partial in its own shared
-// memory, the cluster synchronises, and CTA r of the cluster adds the nch
-// partials of the i-particles l = r, r + nch, ... in chunk order (the chunked
-// form's order and arithmetic, so the results are the same bits) and writes
-// a_i, p_i. No partials in global memory, no fence, no arrival count; a
-// second cluster barrier keeps every CTA's shared memory alive until the
-// others have read it. Launched with the cluster size nch (<= 8) as a launch
+// in distributed shared memory: each CTA stores its partial of i-particle l
+// into the shared memory of the cluster's CTA l % nch, one cluster barrier
+// follows, and CTA r adds the nch partials of its particles l = r, r + nch,
+// ... in chunk order (the chunked form's order and arithmetic, so the results
+// are the same bits) and writes a_i, p_i. No partials in global memory, no
+// fence, no arrival count, and no CTA touches another's shared memory after
+// the barrier. Launched with the cluster size nch (<= 8) as a launch
 // attribute.
 template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedArgs args) {
@@ -808,13 +813,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
     static_assert(kPad % IB == 0, "i-blocks must divide the padding");
     static_assert(WARPS * W * IB * sizeof(float4) <= kFusedJmax * sizeof(JPart),
                   "the cross-warp sums reuse the particle block");
+    static_assert(IB + kMaxClusterChunks <= kClusterSlots, "room for the received partials");
 
     extern __shared__ __align__(128) unsigned char smem[];
     JPart *blk = reinterpret_cast<JPart *>(smem);
     float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after the last block
-    float4 *cpart = reinterpret_cast<float4 *>(smem + kFusedJmax * sizeof(JPart));  // [W][IB]
+    // Received chunk partials of this CTA's particles: [slot][chunk][W].
+    float4 *cpart = reinterpret_cast<float4 *>(smem + kFusedJmax * sizeof(JPart));
     pdl_wait_then_release();
     cg::cluster_group cluster = cg::this_cluster();
+    // Distributed shared memory may be touched only once every CTA of the
+    // cluster runs: arrive now, wait just before the first remote store.
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = args.n, nch = args.nchunks;
@@ -897,6 +907,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
         }
     }
     __syncthreads();
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // every CTA of the cluster runs
+    // This CTA's partial for i-particle l goes straight into the shared
+    // memory of the CTA that owns l (rank l % nch), in the slot of this
+    // chunk: after one cluster barrier every CTA holds all the chunk
+    // partials of its particles locally, and no CTA reads another's shared
+    // memory afterwards (so none has to wait before it exits).
     for (int l = tid; l < IB; l += THREADS) {
         float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
         for (int w = 0; w < WARPS; ++w) {
@@ -917,23 +933,28 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
                 for (int r = 0; r < 4; ++r) S[r] = __fadd_rn(S[r], h[r]);
             }
         }
-        cpart[l] = make_float4(S[0], S[1], S[2], S[3]);
-        if (COMP) cpart[IB + l] = make_float4(-E[0], -E[1], -E[2], -E[3]);
+        // Owner rank l % nch keeps its particles' partials at [slot][chunk][W],
+        // slot = l / nch (fewer than IB / nch + 1 slots).
+        const int owner = l % (int)nch, slot = l / (int)nch;
+        float4 *dst = cluster.map_shared_rank(cpart, owner) + ((int64_t)slot * nch + c) * W;
+        dst[0] = make_float4(S[0], S[1], S[2], S[3]);
+        if (COMP) dst[1] = make_float4(-E[0], -E[1], -E[2], -E[3]);
     }
-    cluster.sync();  // every chunk's partial is in its CTA's shared memory
+    cluster.sync();  // every chunk partial of this CTA's particles has arrived
 
-    // CTA c adds, for i-particles l = c, c + nch, ..., the nch partials in
-    // chunk order (the chunked form's combine) and writes a_i, p_i.
-    for (int l = c + tid * (int)nch; l < IB; l += THREADS * (int)nch) {
+    // CTA c adds, for its i-particles l = c, c + nch, ..., the nch chunk
+    // partials in chunk order (the chunked form's combine) and writes a_i, p_i.
+    for (int slot = tid; slot * (int)nch + c < IB; slot += THREADS) {
+        const int l = slot * (int)nch + c;
         const int64_t gi = b * IB + l;
         if (gi >= n) break;
         float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
         for (int k = 0; k < (int)nch; ++k) {
-            const float4 *src = cluster.map_shared_rank(cpart, k);
-            const float4 hi = src[l];
+            const float4 *src = cpart + ((int64_t)slot * nch + k) * W;
+            const float4 hi = src[0];
             const float h[4] = {hi.x, hi.y, hi.z, hi.w};
             if (COMP) {
-                const float4 lo = src[IB + l];
+                const float4 lo = src[1];
                 const float lw[4] = {lo.x, lo.y, lo.z, lo.w};
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -952,7 +973,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
         args.a[3 * gi + 2] = args.a_scale * __fadd_rn(S[2], E[2]);
         args.p[gi] = args.p_scale * __fadd_rn(S[3], E[3]);
     }
-    cluster.sync();  // the other CTAs have read this CTA's partial
 }
 
 // Synthetic inputs for tuning runs (timing only; values do not matter
@@ -1062,7 +1082,7 @@ constexpr size_t pair_smem() {
 #define NB_FUSED_CL(T, I, J, U, M, N, C)                                                          \
     {{T, I, J, 1, U, M, 0, 0, 63, N, 3}, C,                                                        \
      (const void *)fused_cl_kernel<T / 32, I, J, U, M, (N != 0), C>,                               \
-     kFusedJmax * sizeof(JPart) + (C ? 2 : 1) * 32 * I * sizeof(float4), nullptr,                  \
+     kFusedJmax * sizeof(JPart) + (size_t)(C ? 2 : 1) * kClusterSlots * sizeof(float4), nullptr,    \
      launch_fused_cl<T / 32, I, J, U, M, (N != 0), C>}
 // The same shapes in stream-K form (fused = 2).
 #define NB_FUSED_SK(T, I, J, U, M, N, C)                                                        \
@@ -1263,8 +1283,8 @@ PairPlan make_plan(const PairVariant &v, int64_t n, int resident_ctas) {
     p.smem = v.smem;
     if (v.tile.fused == 3) {
         // Cluster form: one CTA per (i-block, j-chunk), the chunks of an
-        // i-block one cluster of at most kMaxClusterChunks CTAs; no global
-        // partials.
+        // i-block one cluster of at most kMaxClusterChunks CTAs, as many as
+        // the resident CTAs allow; no global partials.
         p.ib = 32 * v.tile.ipt;
         p.npad = round_up(std::max<int64_t>(n, 1), kPad);
         p.nib = (n + p.ib - 1) / p.ib;
