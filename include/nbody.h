@@ -76,8 +76,9 @@ typedef enum nb_status {
  *  NB_COMPENSATED  the tile partials enter the running sum through Kahan
  *                  compensation, the cross-block combine is compensated too,
  *                  and positions held in FP64 (leap-frog state) enter the
- *                  pair arithmetic as FP32 offsets from a per-tile reference
- *                  point. Target: <= 1e-6.
+ *                  pair arithmetic relative to the centre of their bounding
+ *                  box as an exact FP32 grid part plus an FP32 remainder, so
+ *                  that x_i - x_j carries one rounding. Target: <= 1e-6.
  */
 typedef enum nb_mode { NB_PLAIN = 0, NB_COMPENSATED = 1 } nb_mode;
 
@@ -116,10 +117,12 @@ typedef struct nb_ctx nb_ctx;
  * one per resident CTA, so a CTA may finish one i-block and start the next;
  * the last contributing CTA adds the partials in CTA order. `fused` = 3 is
  * the chunked split with the chunks of an i-block launched as one
- * thread-block cluster (at most 8 chunks): the chunk partials stay in each
- * CTA's shared memory and CTA r of the cluster adds, in chunk order, those of
- * every nch-th particle through distributed shared memory (no partials in
- * global memory, no arrival counts); when the GPU cannot hold all of its
+ * thread-block cluster (at most 8 chunks): each CTA sends its partial of
+ * every nch-th particle into the shared memory of the cluster's CTA that owns
+ * it, which adds them in chunk order once they have arrived (no partials in
+ * global memory, no arrival counts); here `minblocks` is the CTAs per SM (1:
+ * the CTA takes a full SM's shared memory, so exactly one runs per SM; 2:
+ * registers held to 128 per thread); when the GPU cannot hold all of its
  * clusters at once, the call runs the chunked form of the same shape. All
  * single-launch shapes are launched with programmatic stream serialization:
  * the next kernel on the stream may be scheduled while the previous one runs,
@@ -391,8 +394,10 @@ nb_status nb_timing_reset(nb_ctx *ctx);
 /* Test hook for the bounded-wait path: with unit >= 0 the pair kernel's
  * producer does not issue the copy of work unit `unit`, so the consumers'
  * bounded wait runs out, the kernel records a timeout and returns, and the
- * next nb_synchronize reports NB_ERR_TIMEOUT. wait_ns sets the wait limit
- * (0 keeps the default of one second). -1 disables. */
+ * next nb_synchronize reports NB_ERR_TIMEOUT. In the cluster form of the
+ * single-launch kernel (nb_tile.fused = 3) CTA `unit` does not send its
+ * partial sums, and the CTAs that own them time out the same way. wait_ns
+ * sets the wait limit (0 keeps the default of one second). -1 disables. */
 nb_status nb_debug_set_fault(nb_ctx *ctx, int64_t unit, int64_t wait_ns);
 
 #ifdef __cplusplus

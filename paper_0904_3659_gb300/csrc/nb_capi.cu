@@ -54,6 +54,7 @@ struct nb_ctx {
     std::map<int, int> tuned[2];           // size class -> variant index
     std::map<const void *, int> occupancy;  // kernel -> resident CTAs per SM
     std::map<std::pair<const void *, int>, int> clusters;  // (kernel, size) -> co-resident clusters
+    std::map<int64_t, int> cluster_pick[2];  // n -> built-in cluster shape chosen for n, per mode
 
     // timing
     bool timing = false;
@@ -213,12 +214,60 @@ int max_active_clusters(nb_ctx *ctx, const PairVariant &v, int size) {
     return num;
 }
 
+// How the cluster form of v would run at n: the pair evaluations on the
+// busiest SM, and whether its clusters all fit on the GPU at once (else it
+// runs as its chunked twin with the same split; a shape without one is not
+// a candidate then).
+struct ClusterLoad {
+    int64_t load;
+    bool fits;
+};
+ClusterLoad cluster_load(nb_ctx *ctx, const PairVariant &v, int64_t n) {
+    const PairPlan p = make_plan(v, n, resident_ctas(ctx, v));
+    const bool fits = max_active_clusters(ctx, v, (int)p.nchunks) >= p.nib;
+    if (!fits && !chunked_twin(v)) return {INT64_MAX, false};
+    const int64_t ctas_per_sm = (p.grid + ctx->sm_count - 1) / ctx->sm_count;
+    const int64_t tiles_per_cta = (p.njt + p.nchunks - 1) / p.nchunks;
+    return {ctas_per_sm * p.ib * tiles_per_cta * v.tile.jtile, fits};
+}
+
+// The built-in shape for n. Where it is a cluster form, the same shape at
+// the other residency (minblocks: 1 or 2 CTAs per SM) replaces it when that
+// gives the busiest SM less work, or as much work with clusters that fit
+// where the built-in one's do not. At N = 7168 two CTAs per SM take clusters
+// of 5 where one CTA per SM allows only 2 (29.8 against 32.2 us per call);
+// at N = 1024 clusters of 8 CTAs fit only at two per SM (5.4 against 7.5 us).
+int default_index(nb_ctx *ctx, int64_t n, bool comp) {
+    const int k = pair_default_index(comp, n);
+    const PairVariant &v = *pair_variant(comp, k);
+    if (v.tile.fused != 3) return k;
+    auto &cache = ctx->cluster_pick[comp ? 1 : 0];
+    auto it = cache.find(n);
+    if (it != cache.end()) return it->second;
+    int best = k;
+    ClusterLoad best_load = cluster_load(ctx, v, n);
+    for (int j = 0; j < pair_variant_count(comp); ++j) {
+        const PairVariant &w = *pair_variant(comp, j);
+        nb_tile t = w.tile;
+        t.minblocks = v.tile.minblocks;
+        if (j == k || w.tile.fused != 3 || !same_tile(t, v.tile)) continue;
+        const ClusterLoad l = cluster_load(ctx, w, n);
+        if (l.load < best_load.load ||
+            (l.load == best_load.load && l.fits && !best_load.fits)) {
+            best = j;
+            best_load = l;
+        }
+    }
+    cache[n] = best;
+    return best;
+}
+
 const PairVariant &choose_variant(nb_ctx *ctx, int64_t n, bool comp) {
     const int m = comp ? 1 : 0;
     if (ctx->has_override[m]) return *pair_variant(comp, ctx->override_idx[m]);
     auto it = ctx->tuned[m].find(size_class(n));
     if (it != ctx->tuned[m].end()) return *pair_variant(comp, it->second);
-    return *pair_variant(comp, pair_default_index(comp, n));
+    return *pair_variant(comp, default_index(ctx, n, comp));
 }
 
 // Enqueue pack -> pair -> combine for one system of n particles already
@@ -269,6 +318,8 @@ nb_status run_force(nb_ctx *ctx, const float *x, const float *m, const JPart *pr
         fa.eps2 = eps * eps;
         fa.a_scale = accel_scale(v.tile.refine);
         fa.p_scale = pot_scale(v.tile.refine);
+        fa.wait_ns = ctx->wait_ns;
+        fa.fault_cta = ctx->fault_unit;
         {
             TimedLaunch t(ctx, K_PAIR, st);
             e = v.launch_fused(fa, plan.grid, plan.smem, st);

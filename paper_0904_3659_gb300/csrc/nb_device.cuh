@@ -36,6 +36,25 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// Address of the object at `p` (this CTA's shared memory) in the shared
+// memory of CTA `rank` of the cluster, as a shared::cluster address.
+__device__ __forceinline__ uint32_t cluster_map(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+// 16-byte store into another CTA's shared memory (shared::cluster address,
+// 16-byte aligned) that signals its bytes to that CTA's mbarrier `rbar`
+// (also a shared::cluster address, in the same CTA) as transaction bytes.
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, float4 v, uint32_t rbar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::
+            "r"(raddr),
+        "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
+        : "memory");
+}
+
 // One-dimensional bulk copy global -> shared through the tensor memory
 // accelerator; completion is signalled on `bar` as transaction bytes.
 // Both addresses must be 16-byte aligned and `bytes` a multiple of 16.

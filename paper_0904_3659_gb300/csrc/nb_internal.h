@@ -82,7 +82,7 @@ struct FusedArgs {
                            //   form), [grid][maxseg][words][ib] (stream-K form)
     int64_t partial_len;   // float4 entries of partial (debug build)
     int *counters;         // [nib] arrivals per i-block; zero between launches
-    int *err;              // device error word (debug build)
+    int *err;              // device error word (timeouts of the cluster form; debug build)
     int64_t nib;
     int64_t njt;           // j-tiles covering n
     int64_t nchunks;       // chunked form: j-chunks (CTAs) per i-block
@@ -91,6 +91,8 @@ struct FusedArgs {
     float a_scale, p_scale;
     int64_t units;         // stream-K form: (i-block, j-tile) units, nib * njt
     int64_t maxseg;        // stream-K form: most i-blocks one CTA's range touches
+    uint64_t wait_ns;      // cluster form: limit of the wait for the other chunks' partials
+    int64_t fault_cta;     // cluster form test hook: CTA whose partials are never sent (-1: none)
 };
 
 // Arguments of the deterministic cross-CTA combine.

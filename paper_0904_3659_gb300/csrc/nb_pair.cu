@@ -792,14 +792,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
 // work split as fused_kernel -- one CTA per (i-block, j-chunk), all warps on
 // the same i, the chunk's tiles shared among the warps -- but the nch CTAs of
 // an i-block form one thread-block cluster, and the chunks' partial sums meet
-// in distributed shared memory: each CTA stores its partial of i-particle l
-// into the shared memory of the cluster's CTA l % nch, one cluster barrier
-// follows, and CTA r adds the nch partials of its particles l = r, r + nch,
-// ... in chunk order (the chunked form's order and arithmetic, so the results
-// are the same bits) and writes a_i, p_i. No partials in global memory, no
-// fence, no arrival count, and no CTA touches another's shared memory after
-// the barrier. Launched with the cluster size nch (<= 8) as a launch
-// attribute.
+// in distributed shared memory: each CTA sends its partial of i-particle l
+// to the shared memory of the cluster's CTA l % nch (st.async, counted as
+// transaction bytes on that CTA's mbarrier), and CTA r, once its mbarrier
+// has counted every byte sent to it (a bounded wait), adds the nch partials
+// of its particles l = r, r + nch, ... in chunk order (the chunked form's
+// order and arithmetic, so the results are the same bits) and writes a_i,
+// p_i. No partials in global memory, no arrival count, no cluster-wide
+// barrier after the compute: a CTA waits only for the bytes it receives, and
+// every CTA's shared memory outlives the stores into it. Launched with the
+// cluster size nch (<= 8) as a launch attribute.
 template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedArgs args) {
     namespace cg = cooperative_groups;
@@ -820,17 +822,27 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
     float4 *red = reinterpret_cast<float4 *>(smem);  // [WARPS][W][IB], after the last block
     // Received chunk partials of this CTA's particles: [slot][chunk][W].
     float4 *cpart = reinterpret_cast<float4 *>(smem + kFusedJmax * sizeof(JPart));
+    __shared__ uint64_t recv_bar;  // counts the bytes the other chunks send here
     pdl_wait_then_release();
     cg::cluster_group cluster = cg::this_cluster();
-    // Distributed shared memory may be touched only once every CTA of the
-    // cluster runs: arrive now, wait just before the first remote store.
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = args.n, nch = args.nchunks;
     const int64_t b = blockIdx.x / nch;
     const int c = (int)cluster.block_rank();  // = blockIdx.x % nch
     const int64_t t0 = c * args.njt / nch, t1 = (c + 1) * args.njt / nch;  // chunk's tiles
+    if (tid == 0) {
+        // This CTA owns l = c, c + nch, ... < IB; each of the other nch - 1
+        // chunks sends it W float4 per owned particle.
+        const uint32_t owned = (uint32_t)((IB - c + nch - 1) / nch);
+        mbar_init(&recv_bar, 1);
+        mbar_arrive_expect_tx(&recv_bar, owned * (uint32_t)(nch - 1) * W * (uint32_t)sizeof(float4));
+        fence_mbar_init();
+    }
+    // Distributed shared memory may be touched only once every CTA of the
+    // cluster runs and has set up its mbarrier: arrive now, wait just before
+    // the first remote store.
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 
     float2 xi[P], yi[P], zi[P];
 #pragma unroll
@@ -910,9 +922,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // every CTA of the cluster runs
     // This CTA's partial for i-particle l goes straight into the shared
     // memory of the CTA that owns l (rank l % nch), in the slot of this
-    // chunk: after one cluster barrier every CTA holds all the chunk
-    // partials of its particles locally, and no CTA reads another's shared
-    // memory afterwards (so none has to wait before it exits).
+    // chunk; its own particles' partials are stored locally. No CTA reads
+    // another's shared memory.
+    const bool send = (int64_t)blockIdx.x != args.fault_cta;  // test hook
     for (int l = tid; l < IB; l += THREADS) {
         float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
         for (int w = 0; w < WARPS; ++w) {
@@ -936,11 +948,28 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
         // Owner rank l % nch keeps its particles' partials at [slot][chunk][W],
         // slot = l / nch (fewer than IB / nch + 1 slots).
         const int owner = l % (int)nch, slot = l / (int)nch;
-        float4 *dst = cluster.map_shared_rank(cpart, owner) + ((int64_t)slot * nch + c) * W;
-        dst[0] = make_float4(S[0], S[1], S[2], S[3]);
-        if (COMP) dst[1] = make_float4(-E[0], -E[1], -E[2], -E[3]);
+        float4 *dst = cpart + ((int64_t)slot * nch + c) * W;
+        const float4 hi = make_float4(S[0], S[1], S[2], S[3]);
+        const float4 lo = make_float4(-E[0], -E[1], -E[2], -E[3]);
+        if (owner == c) {
+            dst[0] = hi;
+            if (COMP) dst[1] = lo;
+        } else if (send) {
+            const uint32_t raddr = cluster_map(dst, (uint32_t)owner);
+            const uint32_t rbar = cluster_map(&recv_bar, (uint32_t)owner);
+            st_async_v4(raddr, hi, rbar);
+            if (COMP) st_async_v4(raddr + (uint32_t)sizeof(float4), lo, rbar);
+        }
     }
-    cluster.sync();  // every chunk partial of this CTA's particles has arrived
+    // Every chunk partial of this CTA's particles has arrived: the other
+    // chunks' by the mbarrier's byte count (bounded wait; on a timeout the
+    // CTA records it and writes nothing), this CTA's own by the barrier.
+    const bool arrived = mbar_wait_bounded(&recv_bar, 0, args.wait_ns);
+    __syncthreads();
+    if (!arrived) {
+        if (tid == 0) atomicOr(args.err, kErrTimeout);
+        return;
+    }
 
     // CTA c adds, for its i-particles l = c, c + nch, ..., the nch chunk
     // partials in chunk order (the chunked form's combine) and writes a_i, p_i.
@@ -1078,12 +1107,22 @@ constexpr size_t pair_smem() {
      (const void *)fused_kernel<T / 32, I, J, U, M, (N != 0), C>, kFusedJmax * sizeof(JPart), \
      nullptr, launch_fused<T / 32, I, J, U, M, (N != 0), C>}
 // The chunked shapes in cluster form (fused = 3): the particle block plus
-// one CTA partial in shared memory.
+// the received chunk partials in shared memory. Here minblocks is the CTAs
+// per SM: 2 holds the registers to 128 per thread; 1 requests
+// kClusterOneSmSmem, so that exactly one CTA runs per SM whatever the
+// register count (at N = 4096, 32 clusters of 4 CTAs on 128 SMs: 11.0 us per
+// call, against 11.3 us when the 128-register kernel put two CTAs on some
+// SMs and none on others).
+constexpr size_t kClusterOneSmSmem = 120 * 1024;
+static_assert(kClusterOneSmSmem >= kFusedJmax * sizeof(JPart) + 2 * kClusterSlots * sizeof(float4) &&
+                  kClusterOneSmSmem <= 227 * 1024,
+              "one CTA's shared memory: room for the cluster form, more than half an SM's");
 #define NB_FUSED_CL(T, I, J, U, M, N, C)                                                          \
     {{T, I, J, 1, U, M, 0, 0, 63, N, 3}, C,                                                        \
      (const void *)fused_cl_kernel<T / 32, I, J, U, M, (N != 0), C>,                               \
-     kFusedJmax * sizeof(JPart) + (size_t)(C ? 2 : 1) * kClusterSlots * sizeof(float4), nullptr,    \
-     launch_fused_cl<T / 32, I, J, U, M, (N != 0), C>}
+     (M) == 1 ? kClusterOneSmSmem                                                                   \
+              : kFusedJmax * sizeof(JPart) + (size_t)(C ? 2 : 1) * kClusterSlots * sizeof(float4), \
+     nullptr, launch_fused_cl<T / 32, I, J, U, M, (N != 0), C>}
 // The same shapes in stream-K form (fused = 2).
 #define NB_FUSED_SK(T, I, J, U, M, N, C)                                                        \
     {{T, I, J, 1, U, M, 0, 0, 63, N, 2}, C,                                                        \
@@ -1136,6 +1175,8 @@ static const PairVariant kPlain[] = {
     NB_FUSED_SK(128, 4, 32, 4, 1, 0, false),
     NB_FUSED_CL(256, 4, 32, 4, 1, 0, false),
     NB_FUSED_CL(256, 2, 32, 4, 1, 0, false),
+    NB_FUSED_CL(256, 4, 32, 4, 2, 0, false),
+    NB_FUSED_CL(256, 2, 32, 4, 2, 0, false),
 };
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
@@ -1165,6 +1206,8 @@ static const PairVariant kComp[] = {
     NB_FUSED_SK(128, 4, 32, 4, 1, 0, true),
     NB_FUSED_CL(256, 4, 32, 4, 1, 0, true),
     NB_FUSED_CL(256, 2, 32, 4, 1, 0, true),
+    NB_FUSED_CL(256, 4, 32, 4, 2, 0, true),
+    NB_FUSED_CL(256, 2, 32, 4, 2, 0, true),
 };
 // HL variants (compensated, positions from FP64 state as HL records), with
 // and without the potential, for large and for small n.
@@ -1248,14 +1291,17 @@ int pair_default_unfused_index(bool comp, int64_t n) {
 }
 
 // Single-launch shapes by size (GB300, whole calls, plain / compensated):
-// the cluster form below kChunkedMaxN (N = 4096: 11.9 / 12.1 us against
-// 12.6 / 13.3 for the chunked form and 30.7 for pack + pair + combine; N =
-// 2048: 6.0 against 7.0), the stream-K form from there to kFusedMaxN (N =
-// 12288: 73.8 / 77.5 us against 92.2 / 94.4 us for the best packed shapes;
-// N = 16384: 129.0 / 133.5 against 137.2 / 141.3 us), the packed shapes
-// above (N = 24576: stream-K 279.0 / 290.5 us against 280.5 / 280.7).
+// the cluster form below kChunkedMaxN, 2 i per lane below kClusterWideMinN
+// (N = 2048: 5.8 / 5.7 us against 7.1 / 7.5 with 4) and 4 from there (N =
+// 3072: 8.6 / 9.2 us against 9.2 / 9.9 with 2, whose clusters of 3 do not
+// all fit; N = 4096: 11.0 / 11.7 against 12.6 / 13.3 for the chunked form and
+// 30.7 for pack + pair + combine), the stream-K form from there to
+// kFusedMaxN (N = 12288: 73.8 / 77.5 us against 92.2 / 94.4 us for the best
+// packed shapes; N = 16384: 129.0 / 133.5 against 137.2 / 141.3 us), the
+// packed shapes above (N = 24576: stream-K 279.0 / 290.5 us against 280.5 /
+// 280.7).
 constexpr int64_t kChunkedMaxN = (int64_t)1 << 13;
-constexpr int64_t kClusterWideMinN = (int64_t)1 << 12;
+constexpr int64_t kClusterWideMinN = (int64_t)3 << 10;
 constexpr int64_t kFusedMaxN = (int64_t)3 << 13;
 
 bool fused_candidate(int64_t n) { return n < (int64_t)1 << 16; }
@@ -1265,7 +1311,8 @@ int pair_default_index(bool comp, int64_t n) {
     constexpr int R = kDefaultRefine;
     // Below kChunkedMaxN the cluster form (the chunked split, partials met in
     // distributed shared memory; it runs as the chunked form when its
-    // clusters do not fit at once): 2 i per lane below 4096, 4 from there.
+    // clusters do not fit at once), one CTA per SM: 2 i per lane below
+    // kClusterWideMinN, 4 from there.
     static const nb_tile cl2{256, 2, 32, 1, 4, 1, 0, 0, 63, R, 3};
     static const nb_tile cl4{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 3};
     static const nb_tile streamk{256, 4, 32, 1, 4, 1, 0, 0, 63, R, 2};

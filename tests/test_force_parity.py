@@ -163,9 +163,10 @@ def test_fused_shapes(nb, ctx, oracle_mod, mode):
     eps = np.float32(1.0 / 64)
     cases = []
     # 20000: a stream-K CTA's range can touch three i-blocks (and the cluster
-    # form falls to one CTA per cluster); 4096 and 8191: the chunked and
-    # cluster forms' workload and their largest built-in size.
-    for n in (1, 200, 3001, 4096, 8191, 9000, 20000):
+    # form falls to one CTA per cluster); 4096, 7168 and 8191: the chunked and
+    # cluster forms' workload, a size where two CTAs per SM take larger
+    # clusters than one, and their largest built-in size.
+    for n in (1, 200, 3001, 4096, 7168, 8191, 9000, 20000):
         x32, m32 = plummer32(n, seed=100 + n)
         cases.append((n, x32, m32, oracle_mod.force(x32, m32, eps)))
     try:
@@ -335,6 +336,40 @@ def test_bounded_wait_reports_timeout_and_context_survives(nb, ctx, oracle_mod, 
     ra, rp, ramag = oracle_mod.force(x32, m32, eps)
     ea, ep = rel_errors(a, p, ra, rp, ramag)
     assert ea.max() <= 1e-5 and ep.max() <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cluster_form_bounded_wait_reports_timeout(nb, ctx, oracle_mod, mode):
+    # In the cluster form one CTA does not send its partial sums (test hook),
+    # so the CTAs that own them wait out their bounded wait (0.2 s here),
+    # record a timeout and write nothing; nb_synchronize reports it. Nothing
+    # hangs or faults, and the next call on the same context is correct.
+    x32, m32 = plummer32(4096, seed=0)
+    eps = np.float32(0.01)
+    tile = [t for t in nb.nb_list_tiles(mode) if t.fused == 3 and t.ipt == 4][0]
+    nb.nb_set_tile(ctx, mode, tile)
+    try:
+        import torch
+        dev = torch.device("cuda:0")
+        xt = torch.from_numpy(x32).to(dev)
+        mt = torch.from_numpy(m32).to(dev)
+        a = torch.empty((4096, 3), device=dev)
+        p = torch.empty(4096, device=dev)
+        nb.nb_debug_set_fault(ctx, 1, 200_000_000)
+        try:
+            nb.nb_force(ctx, xt, mt, 4096, eps, a, p, mode)
+            with pytest.raises(nb.NBError) as e:
+                nb.nb_synchronize(ctx)
+            assert e.value.status == nb.NB_ERR_TIMEOUT
+        finally:
+            nb.nb_debug_set_fault(ctx, -1, 0)
+        a, p = gpu_force(nb, ctx, x32, m32, eps, mode)
+    finally:
+        nb.nb_set_tile(ctx, mode, None)
+    ra, rp, ramag = oracle_mod.force(x32, m32, eps)
+    ea, ep = rel_errors(a, p, ra, rp, ramag)
+    tol = 1e-5 if mode == 0 else 1e-6
+    assert ea.max() <= tol and ep.max() <= tol
 
 
 def test_force_host_matches_device(nb, ctx):
