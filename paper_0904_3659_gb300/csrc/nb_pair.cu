@@ -520,14 +520,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs
             const int64_t ibase = b * IB, jbase = t * JT;
             int self0[P], self1[P];
             if (jbase < ibase + IB && ibase < jbase + JT) {
-#pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
-                    self1[q] = self0[q] + 32;
-                }
                 // (unrolled like the other tiles: in-process A/B at N = 4096, compensated
                 // 15.4 -> 14.5 us, plain unchanged)
-                tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+                if constexpr (JT == 32) {
+                    tile_pass_diag32<P, UNR, NEWTON>((int)((jbase - ibase) / 32), lane, T, xi, yi, zi, acc, eps2);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
+                        self1[q] = self0[q] + 32;
+                    }
+                    tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
+                }
             } else {
                 tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
             }
@@ -688,12 +692,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_sk_kernel(const FusedA
                 const int64_t ibase = b * IB, jbase = t * JT;
                 int self0[P], self1[P];
                 if (jbase < ibase + IB && ibase < jbase + JT) {
+                    if constexpr (JT == 32) {
+                        tile_pass_diag32<P, UNR, NEWTON>((int)((jbase - ibase) / 32), lane, T, xi, yi, zi, acc,
+                                                         eps2);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < P; ++q) {
-                        self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
-                        self1[q] = self0[q] + 32;
+                        for (int q = 0; q < P; ++q) {
+                            self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
+                            self1[q] = self0[q] + 32;
+                        }
+                        tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
                     }
-                    tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
                 } else {
                     tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
                 }
@@ -878,12 +887,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fused_cl_kernel(const FusedA
             const int64_t ibase = b * IB, jbase = t * JT;
             int self0[P], self1[P];
             if (jbase < ibase + IB && ibase < jbase + JT) {
+                if constexpr (JT == 32) {
+                    tile_pass_diag32<P, UNR, NEWTON>((int)((jbase - ibase) / 32), lane, T, xi, yi, zi, acc, eps2);
+                } else {
 #pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
-                    self1[q] = self0[q] + 32;
+                    for (int q = 0; q < P; ++q) {
+                        self0[q] = (int)(ibase + (2 * q) * 32 + lane - jbase);
+                        self1[q] = self0[q] + 32;
+                    }
+                    tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
                 }
-                tile_pass<P, JT, UNR, true, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
             } else {
                 tile_pass<P, JT, UNR, false, kMixAll, NEWTON>(T, xi, yi, zi, acc, eps2, self0, self1);
             }

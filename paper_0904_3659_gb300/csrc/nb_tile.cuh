@@ -43,7 +43,13 @@ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
     return PK ? fma2(a, b, c) : make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
 }
 
-template <int P, int JT, int UNR, bool DIAG, int MIX, bool NEWTON, bool POT = true>
+// DK >= 0 (with DIAG) is the lane-diagonal form of a 32-particle tile whose
+// first particle is the thread's i-slot DK (pair DK / 2, half DK % 2) of lane
+// 0, with i-slot k of lane l the particle 32 k + l of the i-block: then only
+// slot DK of the thread meets itself, at jj == self0[0] (the lane), and the
+// mask costs one compare and one select per j instead of two of each per
+// pair.
+template <int P, int JT, int UNR, bool DIAG, int MIX, bool NEWTON, bool POT = true, int DK = -1>
 __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const float2 (&xi)[P],
                                           const float2 (&yi)[P], const float2 (&zi)[P],
                                           float2 (&acc)[P][4], const float2 eps2,
@@ -75,7 +81,13 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
                 u = vmul<PN>(y, t);
             }
             float2 hm = hmj;
-            if (DIAG) {
+            if constexpr (DIAG && DK >= 0) {
+                static_assert(JT == 32 && DK < 2 * P, "the lane-diagonal form needs 32-particle tiles");
+                if (q == DK / 2 && jj == self0[0]) {
+                    if (DK % 2 == 0) hm.x = 0.f;
+                    else hm.y = 0.f;
+                }
+            } else if constexpr (DIAG) {
                 if (jj == self0[q]) hm.x = 0.f;
                 if (jj == self1[q]) hm.y = 0.f;
             }
@@ -86,6 +98,28 @@ __device__ __forceinline__ void tile_pass(const JPart *__restrict__ T, const flo
             acc[q][0] = vfma<PA>(w, dx, acc[q][0]);
             acc[q][1] = vfma<PA>(w, dy, acc[q][1]);
             acc[q][2] = vfma<PA>(w, dz, acc[q][2]);
+        }
+    }
+}
+
+// A diagonal 32-particle tile of the single-launch kernels (i-blocks of
+// 32 * 2P particles, slot k of lane l the block's particle 32 k + l, tiles
+// starting at multiples of 32): the tile starts at the block's particle
+// 32 k, so only slot k of each lane meets itself, at jj == lane. Dispatches
+// to the lane-diagonal form for that slot (k is uniform across the warp).
+template <int P, int UNR, bool NEWTON, int K = 0>
+__device__ __forceinline__ void tile_pass_diag32(int k, int lane, const JPart *__restrict__ T,
+                                                 const float2 (&xi)[P], const float2 (&yi)[P],
+                                                 const float2 (&zi)[P], float2 (&acc)[P][4],
+                                                 const float2 eps2) {
+    if constexpr (K < 2 * P) {
+        if (k == K) {
+            int self0[P], self1[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) self0[q] = self1[q] = lane;
+            tile_pass<P, 32, UNR, true, kMixAll, NEWTON, true, K>(T, xi, yi, zi, acc, eps2, self0, self1);
+        } else {
+            tile_pass_diag32<P, UNR, NEWTON, K + 1>(k, lane, T, xi, yi, zi, acc, eps2);
         }
     }
 }
