@@ -1225,18 +1225,21 @@ static const PairVariant kComp[] = {
 // HL variants (compensated, positions from FP64 state as HL records), with
 // and without the potential, for large and for small n.
 static const PairVariant kHL[2][2] = {
-    {NB_VARIANT_NP(256, 4, 256, 3, 4, 1, 0, 0, 63, true, true, false),   // large n
+    {NB_VARIANT_NP(256, 4, 512, 3, 4, 1, 0, 0, 63, true, true, false),   // large n (the N = 2^16
+                                                                         // leap-frog: 1% faster than 256)
      NB_VARIANT_NP(64, 4, 128, 4, 4, 1, 0, 0, 63, true, true, false)},   // small n
-    {NB_VARIANT_NP(256, 4, 256, 3, 4, 1, 0, 0, 63, true, true, true),
+    {NB_VARIANT_NP(256, 4, 512, 3, 4, 1, 0, 0, 63, true, true, true),
      NB_VARIANT_NP(64, 4, 128, 4, 4, 1, 0, 0, 63, true, true, true)},
 };
-// No-potential twins of the built-in packed shapes (the integrator's force
-// from packed FP64 state) and of the frame shapes, in that order.
+// No-potential twins of the built-in packed plain-mode shapes (the
+// integrator's force from packed FP64 state, and nb_force with p NULL), and
+// of a large-N shape the tuner may pick.
 static const PairVariant kNoPot[] = {
     NB_VARIANT_NP(256, 2, 128, 4, 4, 1, 0, 0, 63, false, false, true),
     NB_VARIANT_NP(64, 4, 128, 4, 4, 1, 0, 0, 63, false, false, true),
     NB_VARIANT_NP(256, 4, 256, 3, 4, 1, 0, 0, 63, false, false, true),
     NB_VARIANT_NP(128, 12, 256, 3, 4, 1, 0, 1, 63, false, false, true),
+    NB_VARIANT_NP(256, 4, 1024, 3, 4, 1, 0, 0, 63, true, false, true),
 };
 static_assert(kDefaultRefine == 0, "the no-potential and HL shapes have no Newton step");
 #undef NB_VARIANT
@@ -1259,9 +1262,9 @@ const PairVariant *chunked_twin(const PairVariant &v) {
 }
 
 const PairVariant *no_pot_twin(const PairVariant &v) {
-    if (v.comp || v.tile.fused) return nullptr;
+    if (v.tile.fused) return nullptr;
     for (const PairVariant &w : kNoPot)
-        if (same_tile(w.tile, v.tile)) return &w;
+        if (w.comp == v.comp && same_tile(w.tile, v.tile)) return &w;
     return nullptr;
 }
 
@@ -1283,16 +1286,20 @@ static int pair_variant_index(bool comp, const nb_tile &t) {
 // Built-in packed (not fused) choices per size class, from the measured shape
 // sweep (GB300, no Newton step): 2 i per thread and 128-particle tiles while
 // the work cannot fill 152 SMs with large i-blocks, then 4 i per thread in
-// 256-thread CTAs; the plain sums from N = 2^17 on take 1024-particle tiles
-// with the Kahan running sum (2572 -> 2640 G-int/s at N = 2^20 against the
-// plain running sum at that shape).
+// 256-thread CTAs. From N = 2^17 on, plain mode takes 1024-particle tiles
+// with the Kahan running sum (N = 2^20: 2639 against 2572 G-int/s for the
+// plain running sum at the same shape); below, 256-particle tiles, whose
+// no-potential twin runs the N = 2^16 leap-frog 0.6% faster than the Kahan
+// shape's (N = 2^16 with the potential: 2491 against 2594, which the tuner
+// picks). From N = 2^15 on, compensated mode takes 512-particle tiles (N =
+// 2^16, 2^20: 2576, 2621 against 2541, 2585 for 256).
 int pair_default_unfused_index(bool comp, int64_t n) {
     constexpr int R = kDefaultRefine;
     static const nb_tile shapes[2][4] = {
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {64, 4, 128, 4, 4, 1, 0, 0, 63, R},
          {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {256, 4, 1024, 3, 4, 1, 0, 0, 63, R}},
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R},
-         {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R}}};
+         {256, 4, 512, 3, 4, 1, 0, 0, 63, R}, {256, 4, 512, 3, 4, 1, 0, 0, 63, R}}};
     static const int idx[2][4] = {
         {pair_variant_index(false, shapes[0][0]), pair_variant_index(false, shapes[0][1]),
          pair_variant_index(false, shapes[0][2]), pair_variant_index(false, shapes[0][3])},
