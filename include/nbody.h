@@ -217,12 +217,11 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
  * p [n_total] FP32 device, out. One persistent pair launch per step; steps
  * after the first are replayed from a CUDA graph when `stream` is not the
  * legacy default stream. In NB_COMPENSATED mode the FP64 positions enter
- * the pair kernel as FP32 offsets from per-tile reference points: each
- * cluster is ordered along the Morton curve of its bounding box (once per
- * call, from the entry positions), every 128 consecutive ordered particles
- * form a tile whose reference point is their FP64 centroid rounded to FP32,
- * and the offsets are formed in FP64, so x_i - x_j loses about 2^-24 times
- * a tile's extent rather than 2^-24 |x|. Asynchronous.
+ * the pair kernel, at every force evaluation, relative to the centre of
+ * their cluster's bounding box, each coordinate as an exact FP32 grid part
+ * (a multiple of a power of two fine enough that the difference of two grid
+ * parts is exact in FP32) plus an FP32 remainder, so x_i - x_j carries one
+ * rounding wherever the cluster sits. Asynchronous.
  */
 nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const float *m,
                                    const int64_t *offsets, int64_t n_clusters, int64_t n_total,
@@ -244,7 +243,9 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
  *                the integrator needs only a, so the force kernels then leave
  *                the potential out (12 instead of 13 FP32 operations per pair)
  * Asynchronous. In NB_COMPENSATED mode the FP64 positions enter the pair
- * kernel as FP32 offsets from per-tile reference points.
+ * kernel relative to the centre of their bounding box (recomputed at every
+ * force evaluation), each coordinate as an exact FP32 grid part plus an FP32
+ * remainder, so x_i - x_j carries one rounding.
  */
 nb_status nb_leapfrog_step(nb_ctx *ctx, double *x, double *v, const float *m, float *a, float *p,
                            int64_t n, float eps, double dt, int nsteps, int a_valid,
