@@ -12,6 +12,7 @@
 // fixed order, so the results do not depend on which CTA pops what.
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include "nb_device.cuh"
@@ -23,6 +24,12 @@ namespace nbk {
 using namespace nbdev;
 
 constexpr int kClusterPad = 128;  // >= every batched i-block and j-tile
+// The batched kernels' i-block (32 lanes x 4 i) and j-tile sizes, fixed so
+// that the planner and the combine divide by constants (batch_prepare checks
+// every compiled shape against them).
+constexpr int kBatchIB = 128, kBatchJT = 128;
+static_assert(kClusterPad % kBatchIB == 0 && kClusterPad % kBatchJT == 0,
+              "i-blocks and j-tiles lie inside one padded cluster");
 constexpr int kPlanThreads = 1024;
 constexpr int kMaxChunks = 4;      // the j-range of an i-block is split into at most this many items
 
@@ -38,28 +45,43 @@ struct BatchPlanArgs {
     int64_t n_total;      // the caller's particle count (offsets[C] must equal it)
     int64_t cap_padded;   // capacity of the padded particle array
     int64_t cap_items;    // capacity of the item list
-    int ib;               // i-block size of the pair kernel
-    int jt;               // j-tile size of the pair kernel
     int64_t *poff;        // [C+1] padded offsets (out)
     int4 *items;          // [cap_items] (cluster, i-block, chunk, chunks) (out)
     int64_t *ibase;       // [C] index of the cluster's first item (out)
     int *nitems;          // item count (out)
     int *err;             // set if the offsets do not fit the capacities
+    int64_t *planned_off; // [C+1] offsets of the plan in poff/items/ibase (in/out)
+    uint32_t *planned_eps;// [C] bits of its eps (in/out)
+    int replan;           // 1: the scratch holds no plan of this (C, n_total)
 };
 
-// Exclusive block-wide scan of one value per thread (kPlanThreads threads).
+// Exclusive block-wide scan of one value per thread (kPlanThreads threads):
+// a shuffle scan within each warp, then one over the warps' totals. On
+// return smem[t] holds thread t's inclusive prefix and *total the block's sum.
 __device__ int64_t block_exclusive_scan(int64_t v, int64_t *smem, int64_t *total) {
-    const int t = threadIdx.x;
-    smem[t] = v;
-    __syncthreads();
-    for (int d = 1; d < kPlanThreads; d <<= 1) {
-        const int64_t add = t >= d ? smem[t - d] : 0;
-        __syncthreads();
-        smem[t] += add;
-        __syncthreads();
+    constexpr int kWarps = kPlanThreads / 32;
+    static_assert(kWarps <= 32, "the warps' totals are scanned by one warp");
+    __shared__ int64_t wsum[kWarps];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    int64_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
     }
-    const int64_t incl = smem[t];
-    *total = smem[kPlanThreads - 1];
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < kWarps ? wsum[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        if (lane < kWarps) wsum[lane] = w;
+    }
+    __syncthreads();
+    const int64_t incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+    smem[t] = incl;
+    *total = wsum[kWarps - 1];
     __syncthreads();
     return incl - v;
 }
@@ -71,6 +93,16 @@ __device__ __forceinline__ int size_class(int64_t psz) {
 __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPlanArgs P) {
     __shared__ int64_t scan[kPlanThreads];
     const int t = threadIdx.x;
+    // The same offsets and eps as the plan already in the scratch (it was
+    // valid, or planned_off[0] would be -1): that plan stands.
+    if (!P.replan) {
+        int diff = 0;
+        for (int64_t c = t; c <= P.C; c += kPlanThreads) {
+            diff |= P.off[c] != P.planned_off[c];
+            if (c < P.C) diff |= __float_as_uint(P.eps[c]) != P.planned_eps[c];
+        }
+        if (!__syncthreads_or(diff)) return;
+    }
     // Offsets must start at 0, never decrease and end at n_total, and every
     // non-empty cluster's eps must be > 0 with eps^2 a finite normal FP32
     // number (as for nb_force); otherwise every cluster is given zero size so
@@ -89,6 +121,7 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPla
         for (int64_t c = t; c <= P.C; c += kPlanThreads) P.poff[c] = 0;
         if (t == 0) {
             *P.nitems = 0;
+            P.planned_off[0] = -1;  // no valid plan in the scratch
             atomicOr(P.err, kErrBatchPlan);
         }
         return;
@@ -113,134 +146,209 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const BatchPla
     __shared__ unsigned long long present;
     if (t == 0) present = 0ull;
     __syncthreads();
+    unsigned long long mine = 0ull;
     for (int64_t c = t; c < P.C; c += kPlanThreads) {
         const int64_t nc = P.off[c + 1] - P.off[c];
         const int64_t psz = nc > 0 ? (nc + kClusterPad - 1) / kClusterPad * kClusterPad : 0;
-        if (psz > 0) atomicOr(&present, 1ull << size_class(psz));
+        if (psz > 0) mine |= 1ull << size_class(psz);
     }
+    for (int d = 16; d > 0; d >>= 1) mine |= __shfl_xor_sync(0xffffffffu, mine, d);
+    if ((t & 31) == 0 && mine) atomicOr(&present, mine);
     __syncthreads();
     const unsigned long long classes = present;
-    // Items, largest size class first; clusters in index order within a class.
+    // Items, largest size class first; clusters in index order within a class,
+    // and (i-block, chunk) in order within a cluster.
     int64_t nit = 0;
     for (int cls = 62; cls >= 0 && fits; --cls) {
         if (!((classes >> cls) & 1ull)) continue;
         for (int64_t base = 0; base < P.C; base += kPlanThreads) {
             const int64_t c = base + t;
-            int64_t cnt = 0, nb = 0, nch = 0;
+            int64_t cnt = 0, nch = 0;
             if (c < P.C) {
                 const int64_t nc = P.off[c + 1] - P.off[c];
                 const int64_t psz = nc > 0 ? (nc + kClusterPad - 1) / kClusterPad * kClusterPad : 0;
                 if (size_class(psz) == cls) {
-                    nb = psz / P.ib;
-                    nch = chunks_of(psz / P.jt);
-                    cnt = nb * nch;
+                    nch = chunks_of(psz / kBatchJT);
+                    cnt = psz / kBatchIB * nch;
                 }
             }
             int64_t total;
             const int64_t ex = block_exclusive_scan(cnt, scan, &total);
             if (cnt) P.ibase[c] = nit + ex;
-            if (nit + total <= P.cap_items)
-                for (int64_t b = 0; b < nb; ++b)
-                    for (int64_t k = 0; k < nch; ++k)
-                        P.items[nit + ex + b * nch + k] = make_int4((int)c, (int)b, (int)k, (int)nch);
+            // Each warp writes the items of its threads' clusters, one
+            // cluster at a time with all 32 lanes (consecutive items, so the
+            // stores coalesce).
+            if (nit + total <= P.cap_items) {
+                const int lane = t & 31;
+                unsigned todo = __ballot_sync(0xffffffffu, cnt > 0);
+                while (todo) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int64_t first = nit + __shfl_sync(0xffffffffu, ex, src);
+                    const int ccnt = (int)__shfl_sync(0xffffffffu, cnt, src);  // <= 4 x i-blocks
+                    const int cn = (int)__shfl_sync(0xffffffffu, nch, src);
+                    const int cc = (int)(base + (t - lane) + src);
+                    for (int q = lane; q < ccnt; q += 32) {
+                        const int bi = q / cn;
+                        P.items[first + q] = make_int4(cc, bi, q - bi * cn, cn);
+                    }
+                }
+            }
             nit += total;
         }
     }
+    const bool ok = fits && nit <= P.cap_items;
     if (t == 0) {
-        const bool ok = fits && nit <= P.cap_items;
         *P.nitems = ok ? (int)nit : 0;
         if (!ok) atomicOr(P.err, kErrBatchPlan);
     }
-}
-
-// Pack cluster blockIdx.x (FP32 or FP64 source, rounded to FP32) into its
-// padded slot.
-constexpr int kPackThreads = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(kPackThreads) batch_pack_kernel(const T *__restrict__ x,
-                                                                  const float *__restrict__ m,
-                                                                  const int64_t *__restrict__ off,
-                                                                  const int64_t *__restrict__ poff,
-                                                                  JPart *__restrict__ jp) {
-    const int64_t c = blockIdx.x;
-    const int64_t o = off[c], po = poff[c], psz = poff[c + 1] - po;
-    const int64_t nc = psz > 0 ? off[c + 1] - o : 0;
-    for (int64_t li = threadIdx.x; li < psz; li += kPackThreads) {
-        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-        if (li < nc) {
-            const int64_t i = o + li;
-            const float px = (float)x[3 * i], py = (float)x[3 * i + 1], pz = (float)x[3 * i + 2];
-            const float hm = -0.5f * m[i];
-            lo = make_float4(-px, -px, -py, -py);
-            hi = make_float4(-pz, -pz, hm, hm);
-        }
-        float4 *dst = reinterpret_cast<float4 *>(jp + po + li);
-        dst[0] = lo;
-        dst[1] = hi;
+    // Remember what this plan was made for (an unusable plan: nothing).
+    for (int64_t c = t; c <= P.C; c += kPlanThreads) {
+        P.planned_off[c] = ok ? P.off[c] : -1;
+        if (c < P.C) P.planned_eps[c] = __float_as_uint(P.eps[c]);
     }
 }
 
-// Compensated mode on FP64 state: cluster blockIdx.x as HL records (two
-// JParts per particle, see kHLRecords), relative to the centre of the
-// cluster's bounding box, on the grid 2^(E-23) set by the box's half-width
-// (all pairs lie inside one cluster, so each cluster has its own frame and
-// grid). Padding rows are inert (zero position and mass).
-__global__ void __launch_bounds__(kPackThreads) batch_pack_hl_kernel(const double *__restrict__ x,
-                                                                     const float *__restrict__ m,
-                                                                     const int64_t *__restrict__ off,
-                                                                     const int64_t *__restrict__ poff,
-                                                                     JPart *__restrict__ jp) {
-    __shared__ double s[6][kPackThreads];
+// The cluster holding padded row s (0 <= s < poff[C]): the largest c with
+// poff[c] <= s (an empty cluster has poff[c] == poff[c + 1]).
+__device__ __forceinline__ int64_t padded_cluster(const int64_t *__restrict__ poff, int64_t C,
+                                                  int64_t s) {
+    int64_t lo = 0, hi = C - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (poff[mid] <= s) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The padded rows are processed in blocks of kClusterPad rows, each inside
+// one cluster: one CTA per block, one thread per row, so every row's loads
+// are in flight at once however the sizes are distributed. Blocks past
+// poff[C] (the capacity bound, or every block when the planner rejected the
+// offsets and left poff zero) do nothing.
+
+// Pack the padded rows (FP32 or FP64 source, rounded to FP32); rows past a
+// cluster's particles are inert (zero position and mass).
+template <typename T>
+__global__ void __launch_bounds__(kClusterPad) batch_pack_kernel(const T *__restrict__ x,
+                                                                 const float *__restrict__ m,
+                                                                 const int64_t *__restrict__ off,
+                                                                 const int64_t *__restrict__ poff,
+                                                                 int64_t C, JPart *__restrict__ jp) {
+    const int64_t s = (int64_t)blockIdx.x * kClusterPad;
+    if (s >= poff[C]) return;
+    const int64_t c = padded_cluster(poff, C, s);
+    const int64_t li = s - poff[c] + threadIdx.x, o = off[c], nc = off[c + 1] - o;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (li < nc) {
+        const int64_t i = o + li;
+        const float px = (float)x[3 * i], py = (float)x[3 * i + 1], pz = (float)x[3 * i + 2];
+        const float hm = -0.5f * m[i];
+        lo = make_float4(-px, -px, -py, -py);
+        hi = make_float4(-pz, -pz, hm, hm);
+    }
+    float4 *dst = reinterpret_cast<float4 *>(jp + s + threadIdx.x);
+    dst[0] = lo;
+    dst[1] = hi;
+}
+
+// Order-preserving map of an FP64 value's bits to a signed 64-bit integer
+// (its own inverse): the bounding box below is reduced with integer min/max,
+// which run at the integer pipe's rate rather than the FP64 pipe's.
+__device__ __forceinline__ long long ordered_key(long long bits) {
+    return bits >= 0 ? bits : bits ^ 0x7fffffffffffffffll;
+}
+
+constexpr int kFrameThreads = 512;
+
+// Compensated mode on FP64 state, first pass: the frame of cluster
+// blockIdx.x, the centre of its bounding box and the grid 2^(E-23) set by
+// the box's half-width (all pairs lie inside one cluster, so each cluster
+// has its own frame): frame[c] = (centre, grid). Positions are finite.
+__global__ void __launch_bounds__(kFrameThreads) batch_frame_kernel(const double *__restrict__ x,
+                                                                    const int64_t *__restrict__ off,
+                                                                    const int64_t *__restrict__ poff,
+                                                                    double4 *__restrict__ frame) {
+    __shared__ long long s[6][kFrameThreads / 32];
     const int64_t c = blockIdx.x;
-    const int t = threadIdx.x;
-    const int64_t o = off[c], po = poff[c], psz = poff[c + 1] - po;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t o = off[c], psz = poff[c + 1] - poff[c];
     const int64_t nc = psz > 0 ? off[c + 1] - o : 0;
     if (psz <= 0) return;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t li = t; li < nc; li += kPackThreads)
+    const long long *xb = reinterpret_cast<const long long *>(x) + 3 * o;
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+#pragma unroll 4
+    for (int64_t li = t; li < nc; li += kFrameThreads)
         for (int k = 0; k < 3; ++k) {
-            lo[k] = fmin(lo[k], x[3 * (o + li) + k]);
-            hi[k] = fmax(hi[k], x[3 * (o + li) + k]);
+            const long long v = ordered_key(xb[3 * li + k]);
+            lo[k] = v < lo[k] ? v : lo[k];
+            hi[k] = v > hi[k] ? v : hi[k];
         }
-    for (int k = 0; k < 3; ++k) {
-        s[k][t] = lo[k];
-        s[3 + k][t] = hi[k];
-    }
+    for (int k = 0; k < 3; ++k)
+        for (int d = 16; d > 0; d >>= 1) {
+            const long long a = __shfl_xor_sync(0xffffffffu, lo[k], d);
+            const long long b = __shfl_xor_sync(0xffffffffu, hi[k], d);
+            lo[k] = a < lo[k] ? a : lo[k];
+            hi[k] = b > hi[k] ? b : hi[k];
+        }
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+            s[k][warp] = lo[k];
+            s[3 + k][warp] = hi[k];
+        }
     __syncthreads();
-    for (int w = kPackThreads / 2; w > 0; w >>= 1) {
-        if (t < w)
-            for (int k = 0; k < 3; ++k) {
-                s[k][t] = fmin(s[k][t], s[k][t + w]);
-                s[3 + k][t] = fmax(s[3 + k][t], s[3 + k][t + w]);
+    if (t == 0) {
+        double cen[3], ext = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            long long l = s[k][0], h = s[3 + k][0];
+            for (int w = 1; w < kFrameThreads / 32; ++w) {
+                l = s[k][w] < l ? s[k][w] : l;
+                h = s[3 + k][w] > h ? s[3 + k][w] : h;
             }
-        __syncthreads();
-    }
-    double cen[3], ext = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        cen[k] = 0.5 * (s[k][0] + s[3 + k][0]);
-        ext = fmax(ext, 0.5 * (s[3 + k][0] - s[k][0]));
-    }
-    const int e = hl_grid_exponent(ext);
-    const double g = ldexp(1.0, e - 23), ginv = ldexp(1.0, 23 - e);
-    for (int64_t li = t; li < psz; li += kPackThreads) {
-        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f}, hm = 0.f;
-        if (li < nc) {
-            const int64_t i = o + li;
-            for (int k = 0; k < 3; ++k) {
-                const double y = x[3 * i + k] - cen[k];
-                const double yh = rint(y * ginv) * g;  // exact: |y| <= 2^e
-                h[k] = (float)yh;
-                l[k] = (float)(y - yh);
-            }
-            hm = -0.5f * m[i];
+            const double dl = __longlong_as_double(ordered_key(l)), dh = __longlong_as_double(ordered_key(h));
+            cen[k] = 0.5 * (dl + dh);
+            ext = fmax(ext, 0.5 * (dh - dl));
         }
-        float4 *dst = reinterpret_cast<float4 *>(jp + kHLRecords * (po + li));
-        dst[0] = make_float4(-h[0], -h[0], -h[1], -h[1]);
-        dst[1] = make_float4(-h[2], -h[2], hm, hm);
-        dst[2] = make_float4(-l[0], -l[0], -l[1], -l[1]);
-        dst[3] = make_float4(-l[2], -l[2], 0.f, 0.f);
+        frame[c] = make_double4(cen[0], cen[1], cen[2], ldexp(1.0, hl_grid_exponent(ext) - 23));
     }
+}
+
+// Second pass: the padded rows as HL records (two JParts per particle, see
+// kHLRecords) in their cluster's frame; padding rows are inert (zero
+// position and mass). Each coordinate y = x - centre (|y| <= 2^E) is split
+// into h, y rounded to a multiple of the grid G (adding and subtracting
+// 1.5 * 2^52 G, whose unit in the last place is G, rounds to the nearest
+// multiple exactly), and the FP32 remainder l = fl32(y - h).
+__global__ void __launch_bounds__(kClusterPad) batch_pack_hl_kernel(const double *__restrict__ x,
+                                                                    const float *__restrict__ m,
+                                                                    const int64_t *__restrict__ off,
+                                                                    const int64_t *__restrict__ poff,
+                                                                    const double4 *__restrict__ frame,
+                                                                    int64_t C, JPart *__restrict__ jp) {
+    const int64_t s = (int64_t)blockIdx.x * kClusterPad;
+    if (s >= poff[C]) return;
+    const int64_t c = padded_cluster(poff, C, s);
+    const int64_t li = s - poff[c] + threadIdx.x, o = off[c], nc = off[c + 1] - o;
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f}, hm = 0.f;
+    if (li < nc) {
+        const double4 f = frame[c];
+        const double cen[3] = {f.x, f.y, f.z};
+        const double magic = 6755399441055744.0 * f.w;  // 1.5 * 2^52 * G
+        const int64_t i = o + li;
+        for (int k = 0; k < 3; ++k) {
+            const double y = __dsub_rn(x[3 * i + k], cen[k]);
+            const double yh = __dsub_rn(__dadd_rn(y, magic), magic);
+            h[k] = (float)yh;
+            l[k] = (float)__dsub_rn(y, yh);
+        }
+        hm = -0.5f * m[i];
+    }
+    float4 *dst = reinterpret_cast<float4 *>(jp + kHLRecords * (s + threadIdx.x));
+    dst[0] = make_float4(-h[0], -h[0], -h[1], -h[1]);
+    dst[1] = make_float4(-h[2], -h[2], hm, hm);
+    dst[2] = make_float4(-l[0], -l[0], -l[1], -l[1]);
+    dst[3] = make_float4(-l[2], -l[2], 0.f, 0.f);
 }
 
 struct BatchArgs {
@@ -475,57 +583,59 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
 
 // Per particle: add the chunk sums of its (cluster, i-block) in chunk order
 // and remove the factors the pair sums carry (accel_scale, pot_scale of the
-// batched kernel's refine setting). One block per cluster.
+// batched kernel's refine setting). One CTA per padded i-block of kBatchIB
+// rows (which divides kClusterPad, so the block lies inside one cluster), one
+// thread per particle.
 template <bool COMP>
 __global__ void batch_combine_kernel(const float4 *__restrict__ partial,
                                      const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
-                                     const int64_t *__restrict__ ibase, int ib, int jt,
+                                     const int64_t *__restrict__ ibase, int64_t C,
                                      float *__restrict__ a, float *__restrict__ p,
                                      int64_t partial_len, int64_t n_total, int *err) {
-    const int64_t c = blockIdx.x;
     // poff holds the validated padded sizes: all zero when the planner
     // rejected the offsets, so nothing is written for an invalid batch, and
     // a valid cluster's real size never exceeds its padded size.
+    constexpr int ib = kBatchIB;
+    const int64_t s = (int64_t)blockIdx.x * ib;
+    if (s >= poff[C]) return;
+    const int64_t c = padded_cluster(poff, C, s);
     const int64_t psz = poff[c + 1] - poff[c];
-    if (psz <= 0) return;
     const int64_t o = off[c];
     const int64_t nc = off[c + 1] - o < psz ? off[c + 1] - o : psz;
-    if (nc <= 0) return;
-    const int64_t nch = chunks_of(psz / jt);
-    for (int64_t li = threadIdx.x; li < nc; li += blockDim.x) {
-        const int64_t b = li / ib, w = li - b * ib;
-        const int64_t first = ibase[c] + b * nch;
-        float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int64_t k = 0; k < nch; ++k) {
-            const int64_t base = (first + k) * (COMP ? 2 : 1) * ib + w;
-            if (!NB_IN(err, 14, base + (COMP ? ib : 0) < partial_len)) continue;
-            const float4 hi = partial[base];
-            const float h[4] = {hi.x, hi.y, hi.z, hi.w};
-            if (COMP) {
-                const float4 lo = partial[base + ib];
-                const float l[4] = {lo.x, lo.y, lo.z, lo.w};
+    const int64_t b = (s - poff[c]) / ib, w = threadIdx.x, li = b * ib + w;
+    if (li >= nc) return;
+    const int64_t nch = chunks_of(psz / kBatchJT);
+    const int64_t first = ibase[c] + b * nch;
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t k = 0; k < nch; ++k) {
+        const int64_t base = (first + k) * (COMP ? 2 : 1) * ib + w;
+        if (!NB_IN(err, 14, base + (COMP ? ib : 0) < partial_len)) continue;
+        const float4 hi = partial[base];
+        const float h[4] = {hi.x, hi.y, hi.z, hi.w};
+        if (COMP) {
+            const float4 lo = partial[base + ib];
+            const float l[4] = {lo.x, lo.y, lo.z, lo.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    // TwoSum(S, h) then add the chunk's lost low part (h - l is its value)
-                    const float t = __fadd_rn(S[q], h[q]);
-                    const float bp = __fsub_rn(t, S[q]);
-                    const float e = __fadd_rn(__fsub_rn(S[q], __fsub_rn(t, bp)), __fsub_rn(h[q], bp));
-                    S[q] = t;
-                    E[q] = __fadd_rn(E[q], __fsub_rn(e, l[q]));
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) S[q] = __fadd_rn(S[q], h[q]);
+            for (int q = 0; q < 4; ++q) {
+                // TwoSum(S, h) then add the chunk's lost low part (h - l is its value)
+                const float t = __fadd_rn(S[q], h[q]);
+                const float bp = __fsub_rn(t, S[q]);
+                const float e = __fadd_rn(__fsub_rn(S[q], __fsub_rn(t, bp)), __fsub_rn(h[q], bp));
+                S[q] = t;
+                E[q] = __fadd_rn(E[q], __fsub_rn(e, l[q]));
             }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) S[q] = __fadd_rn(S[q], h[q]);
         }
-        const int64_t gi = o + li;
-        if (!NB_IN(err, 14, gi >= 0 && gi < n_total)) continue;
-        constexpr float as = accel_scale(kDefaultRefine), ps = pot_scale(kDefaultRefine);
-        a[3 * gi + 0] = as * __fadd_rn(S[0], E[0]);
-        a[3 * gi + 1] = as * __fadd_rn(S[1], E[1]);
-        a[3 * gi + 2] = as * __fadd_rn(S[2], E[2]);
-        p[gi] = ps * __fadd_rn(S[3], E[3]);
     }
+    const int64_t gi = o + li;
+    if (!NB_IN(err, 14, gi >= 0 && gi < n_total)) return;
+    constexpr float as = accel_scale(kDefaultRefine), ps = pot_scale(kDefaultRefine);
+    a[3 * gi + 0] = as * __fadd_rn(S[0], E[0]);
+    a[3 * gi + 1] = as * __fadd_rn(S[1], E[1]);
+    a[3 * gi + 2] = as * __fadd_rn(S[2], E[2]);
+    p[gi] = ps * __fadd_rn(S[3], E[3]);
 }
 
 // Leap-frog pieces that do not pack (the batched pack follows them).
@@ -600,7 +710,9 @@ enum BSlot : int {
     B_ITEMS = SLOT_BATCH_ITEMS,
     B_NITEMS = SLOT_BATCH_COUNT,
     B_PART = SLOT_BATCH_PART,
-    B_IBASE = SLOT_BATCH_IBASE
+    B_IBASE = SLOT_BATCH_IBASE,
+    B_FRAME = SLOT_BATCH_FRAME,
+    B_PLANNED = SLOT_BATCH_PLANNED
 };
 
 void *bslot(nb_ctx *ctx, int k) { return ctx_ext(ctx).buf[k]; }
@@ -636,6 +748,8 @@ nb_status batch_prepare(nb_ctx *ctx, int64_t C, int64_t n_total, bool comp, bool
                         BatchPlanHost *out) {
     const BatchVariant &v = kBatch[hl ? 2 : comp ? 1 : 0];
     const int ib = 32 * v.ipt;  // one warp per work item
+    if (ib != kBatchIB || v.jtile != kBatchJT)
+        return fail(ctx, NB_ERR_ARG, "batched shape does not match the planner's block sizes");
     out->v = &v;
     out->n_total = n_total;
     out->cap_padded = n_total + C * (int64_t)kClusterPad;
@@ -667,16 +781,28 @@ nb_status batch_plan(nb_ctx *ctx, const int64_t *offsets, const float *eps, int6
     P.n_total = h.n_total;
     P.cap_padded = h.cap_padded;
     P.cap_items = h.cap_items;
-    P.ib = 32 * h.v->ipt;
-    P.jt = h.v->jtile;
     P.poff = static_cast<int64_t *>(bslot(ctx, B_POFF));
     P.items = static_cast<int4 *>(bslot(ctx, B_ITEMS));
     P.ibase = static_cast<int64_t *>(bslot(ctx, B_IBASE));
     P.nitems = static_cast<int *>(bslot(ctx, B_NITEMS));
     P.err = ctx_err_word(ctx);
+    // The previous plan is reused when the offsets and eps are the same
+    // values (checked on the device); it can only be in the scratch if the
+    // last plan was made for the same (C, n_total), which sized the scratch.
+    ExtState &es = ctx_ext(ctx);
+    nb_status rs = bensure(ctx, B_PLANNED, (size_t)(C + 1) * sizeof(int64_t) + (size_t)C * sizeof(uint32_t));
+    if (rs != NB_OK) return rs;
+    P.planned_off = static_cast<int64_t *>(bslot(ctx, B_PLANNED));
+    P.planned_eps = reinterpret_cast<uint32_t *>(P.planned_off + C + 1);
+    P.replan = !(es.plan_clusters == C && es.plan_total == h.n_total);
     batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(P);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch plan launch");
+    if (e != cudaSuccess) {
+        es.plan_clusters = es.plan_total = -1;
+        return cuda_fail(ctx, e, "batch plan launch");
+    }
+    es.plan_clusters = C;
+    es.plan_total = h.n_total;
     return NB_OK;
 }
 
@@ -706,14 +832,15 @@ nb_status batch_pair(nb_ctx *ctx, const int64_t *offsets, int64_t C, const float
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched pair kernel launch");
     const int ib = 32 * h.v->ipt;
+    const unsigned nblk = (unsigned)((h.cap_padded + ib - 1) / ib);
     if (h.v->comp)
-        batch_combine_kernel<true><<<(unsigned)C, 256, 0, st>>>(
-            A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), ib,
-            h.v->jtile, a, p, A.partial_len, h.n_total, A.err);
+        batch_combine_kernel<true><<<nblk, ib, 0, st>>>(
+            A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), C, a, p,
+            A.partial_len, h.n_total, A.err);
     else
-        batch_combine_kernel<false><<<(unsigned)C, 256, 0, st>>>(
-            A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), ib,
-            h.v->jtile, a, p, A.partial_len, h.n_total, A.err);
+        batch_combine_kernel<false><<<nblk, ib, 0, st>>>(
+            A.partial, offsets, A.poff, static_cast<const int64_t *>(bslot(ctx, B_IBASE)), C, a, p,
+            A.partial_len, h.n_total, A.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "batched combine launch");
     return NB_OK;
 }
@@ -742,8 +869,8 @@ nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const in
     if ((st = batch_prepare(ctx, n_clusters, n_total, mode == NB_COMPENSATED, false, &h)) != NB_OK)
         return st;
     if ((st = batch_plan(ctx, offsets, eps, n_clusters, h, s)) != NB_OK) return st;
-    batch_pack_kernel<float><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(
-        x, m, offsets, static_cast<const int64_t *>(bslot(ctx, B_POFF)),
+    batch_pack_kernel<float><<<(unsigned)(h.cap_padded / kClusterPad), kClusterPad, 0, s>>>(
+        x, m, offsets, static_cast<const int64_t *>(bslot(ctx, B_POFF)), n_clusters,
         static_cast<JPart *>(bslot(ctx, B_JP)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched pack launch");
@@ -773,12 +900,19 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
     const unsigned nb3 = (unsigned)((3 * n_total + 255) / 256);
     cudaError_t e;
 
+    double4 *frame = nullptr;
+    if (hl) {
+        if ((st = bensure(ctx, B_FRAME, (size_t)n_clusters * sizeof(double4))) != NB_OK) return st;
+        frame = static_cast<double4 *>(bslot(ctx, B_FRAME));
+    }
+    const unsigned npack = (unsigned)(h.cap_padded / kClusterPad);
     auto force = [&]() -> nb_status {
-        if (hl)
-            batch_pack_hl_kernel<<<(unsigned)n_clusters, kPackThreads, 0, s>>>(x, m, offsets, poff, jp);
-        else
-            batch_pack_kernel<double><<<(unsigned)n_clusters, kPackThreads, 0, s>>>(x, m, offsets,
-                                                                                   poff, jp);
+        if (hl) {
+            batch_frame_kernel<<<(unsigned)n_clusters, kFrameThreads, 0, s>>>(x, offsets, poff, frame);
+            batch_pack_hl_kernel<<<npack, kClusterPad, 0, s>>>(x, m, offsets, poff, frame, n_clusters, jp);
+        } else {
+            batch_pack_kernel<double><<<npack, kClusterPad, 0, s>>>(x, m, offsets, poff, n_clusters, jp);
+        }
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(ctx, le, "batched pack launch");
         return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);

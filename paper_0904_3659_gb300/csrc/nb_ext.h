@@ -27,6 +27,8 @@ enum ExtSlot : int {
     SLOT_VJP_PART,      // VJP partial sums
     SLOT_HL_BOX,        // bounding-box partials of FP64 positions (HL packing)
     SLOT_ADJOINT,       // leap-frog adjoint: replayed state, position history, VJP operands
+    SLOT_BATCH_FRAME,   // per-cluster HL frames (centre, grid) of the batched leap-frog
+    SLOT_BATCH_PLANNED, // the offsets and eps the current batched plan was made for
     SLOT_COUNT
 };
 
@@ -35,6 +37,8 @@ struct ExtState {
     void *buf[kSlots] = {};
     size_t cap[kSlots] = {};
     int vjp_idx = -1;  // VJP shape forced by nb_set_vjp_tile (-1: built-in)
+    // (n_clusters, n_total) of the batched plan in the scratch (-1: none).
+    int64_t plan_clusters = -1, plan_total = -1;
 };
 void ext_release(ExtState &s);
 

@@ -131,6 +131,46 @@ def test_invalid_offsets_rejected_without_writes(nb, ctx):
     nb.nb_synchronize(ctx)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plan_follows_offsets_and_eps_changed_in_place(nb, ctx, oracle_mod, mode):
+    # The context keeps its last batched plan and reuses it while the
+    # offsets and eps hold the same values; the same device arrays rewritten
+    # between calls (same cluster count and particle total), made invalid and
+    # then restored must each be planned afresh.
+    import torch
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(21)
+    n = 3000
+    x32 = rng.normal(size=(n, 3)).astype(np.float32)
+    m32 = rng.uniform(0.5, 1.5, size=n).astype(np.float32) / n
+    xt = torch.from_numpy(x32).to(dev)
+    mt = torch.from_numpy(m32).to(dev)
+    off = torch.empty(4, dtype=torch.int64, device=dev)
+    eps = torch.empty(3, dtype=torch.float32, device=dev)
+    a = torch.empty((n, 3), device=dev)
+    p = torch.empty(n, device=dev)
+    cases = [([0, 700, 2100, 3000], [0.05, 0.1, 0.02]),
+             ([0, 1500, 1600, 3000], [0.05, 0.1, 0.02]),   # boundaries moved
+             ([0, 1500, 1600, 3000], [0.01, 0.2, 0.03]),   # eps changed
+             ([0, 2000, 1600, 3000], [0.01, 0.2, 0.03]),   # invalid: decreasing
+             ([0, 1500, 1600, 3000], [0.01, 0.2, 0.03]),   # restored
+             ([0, 700, 2100, 3000], [0.05, 0.1, 0.02])]
+    for o, e in cases:
+        off.copy_(torch.tensor(o, dtype=torch.int64))
+        eps.copy_(torch.tensor(e, dtype=torch.float32))
+        a.fill_(float("nan"))
+        p.fill_(float("nan"))
+        nb.nb_force_batched(ctx, xt, mt, off, 3, n, eps, a, p, mode)
+        if any(o[k + 1] < o[k] for k in range(3)):
+            with pytest.raises(nb.NBError) as err:
+                nb.nb_synchronize(ctx)
+            assert err.value.status == nb.NB_ERR_ARG
+            continue
+        nb.nb_synchronize(ctx)
+        check_clusters(oracle_mod, x32, m32, np.array(o), np.array(e, np.float32),
+                       a.cpu().numpy(), p.cpu().numpy(), TOL[mode])
+
+
 def test_batched_leapfrog_matches_single_cluster_calls(nb, ctx):
     # 32 graph-replayed KDK steps of a batch equal, cluster by cluster, the
     # single-system integrator's steps (same arithmetic per pair; the pair
