@@ -86,7 +86,11 @@ struct VjpArgs {
     int64_t npad, partial_len;  // extents (debug-build bounds checks)
 };
 
-template <int P, int JT, int UNR, bool DIAG, bool GP>
+// DIAG with DS >= 0: the lane-diagonal form. Only i-slot DS of the thread
+// (pair DS / 2, half DS % 2) meets itself in this tile, at jj == self0[0]
+// (a warp-uniform offset plus the lane), so the self term costs one compare
+// and one select per j.
+template <int P, int JT, int UNR, bool DIAG, bool GP, int DS = -1>
 __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const float2 (&xi)[P],
                                          const float2 (&yi)[P], const float2 (&zi)[P],
                                          const float2 (&g3x)[P], const float2 (&g3y)[P],
@@ -113,7 +117,13 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
             s = fma2(dz, dz, s);
             const float2 y = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
             float2 u = kVNewton ? mul2(y, fma2(s, mul2(y, y), m3)) : y;  // -2 y1, or y
-            if (DIAG) {
+            if constexpr (DIAG && DS >= 0) {
+                static_assert(DS < 2 * P, "slot index");
+                if (q == DS / 2 && jj == self0[0]) {
+                    if (DS % 2 == 0) u.x = 0.f;
+                    else u.y = 0.f;
+                }
+            } else if constexpr (DIAG) {
                 if (jj == self0[q]) u.x = 0.f;
                 if (jj == self1[q]) u.y = 0.f;
             }
@@ -138,6 +148,38 @@ __device__ __forceinline__ void vjp_tile(const VPart *__restrict__ T, const floa
             acc[q][6] = fma2(u3, gzj, acc[q][6]);
             acc[q][7] = GP ? fma2(gp4nj, u, fma2(dgj, u3, acc[q][7])) : fma2(dgj, u3, acc[q][7]);
         }
+    }
+}
+
+// A tile that holds some of the thread's own i-particles. Slot k of thread
+// tid is particle ibase + k * THREADS + tid, and the tile starts at jbase;
+// with THREADS and JT multiples of 32 and the tile at most THREADS wide, at
+// most one slot of a warp meets the tile, all 32 lanes at once, at
+// jj = (that slot's first particle - jbase) + lane. The warp runs the
+// lane-diagonal form for that slot, or the plain form when none meets it.
+template <int THREADS, int P, int JT, int UNR, bool GP, int K = 0>
+__device__ __forceinline__ void vjp_tile_diag(int64_t ibase, int64_t jbase, int tid,
+                                              const VPart *__restrict__ T, const float2 (&xi)[P],
+                                              const float2 (&yi)[P], const float2 (&zi)[P],
+                                              const float2 (&g3x)[P], const float2 (&g3y)[P],
+                                              const float2 (&g3z)[P], const float2 (&nm3)[P],
+                                              const float2 (&gp4)[P], const float2 (&nm)[P],
+                                              float2 (&acc)[P][8], const float2 eps2) {
+    static_assert(THREADS % 32 == 0 && JT % 32 == 0 && JT <= THREADS, "warp-aligned slots");
+    int self0[P], self1[P];
+    if constexpr (K < 2 * P) {
+        const int64_t first = ibase + (int64_t)K * THREADS + (tid & ~31);  // the warp's slot-K block
+        if (first < jbase + JT && jbase < first + 32) {
+            self0[0] = (int)(first - jbase) + (tid & 31);
+            vjp_tile<P, JT, UNR, true, GP, K>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2,
+                                              self0, self1);
+        } else {
+            vjp_tile_diag<THREADS, P, JT, UNR, GP, K + 1>(ibase, jbase, tid, T, xi, yi, zi, g3x, g3y,
+                                                          g3z, nm3, gp4, nm, acc, eps2);
+        }
+    } else {
+        vjp_tile<P, JT, UNR, false, GP>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
+                                        self1);
     }
 }
 
@@ -267,13 +309,18 @@ __global__ void __launch_bounds__(THREADS, MINB) vjp_kernel(const VjpArgs args) 
         const int64_t ibase = b * IB, jbase = jt * JT;
         int self0[P], self1[P];
         if (jbase < ibase + IB && ibase < jbase + JT) {
+            if constexpr (JT <= THREADS) {
+                vjp_tile_diag<THREADS, P, JT, UNR, GP>(ibase, jbase, tid, T, xi, yi, zi, g3x, g3y, g3z,
+                                                       nm3, gp4, nm, acc, eps2);
+            } else {
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
-                self1[q] = self0[q] + THREADS;
+                for (int q = 0; q < P; ++q) {
+                    self0[q] = (int)(ibase + (2 * q) * THREADS + tid - jbase);
+                    self1[q] = self0[q] + THREADS;
+                }
+                vjp_tile<P, JT, 1, true, GP>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2,
+                                             self0, self1);
             }
-            vjp_tile<P, JT, 1, true, GP>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2, self0,
-                                         self1);
         } else {
             vjp_tile<P, JT, UNR, false, GP>(T, xi, yi, zi, g3x, g3y, g3z, nm3, gp4, nm, acc, eps2,
                                          self0, self1);
@@ -380,21 +427,29 @@ constexpr size_t vjp_smem() {
      vjp_smem<T, I, J, S, A>(),                                                             \
      {launch_vjp<T, I, J, S, U, A, false, M>, launch_vjp<T, I, J, S, U, A, true, M>}}
 #define NB_VJP(T, I, J, S, U, A) NB_VJP_M(T, I, J, S, U, A, 1)
+// One packed pair per thread at up to 128 registers: two 256-thread CTAs (or
+// four of 128) per SM; the diagonal tiles' lane-diagonal form would
+// otherwise take the with-gradient-on-p kernels to 130 and one CTA.
 const VjpVariant kVjp[] = {
-    NB_VJP(256, 2, 128, 3, 2, 0), NB_VJP(256, 2, 128, 3, 4, 0), NB_VJP(512, 2, 128, 3, 2, 0),
-    NB_VJP(128, 2, 128, 3, 2, 0), NB_VJP(256, 2, 256, 3, 2, 0), NB_VJP(64, 4, 128, 3, 2, 0),
-    NB_VJP(128, 4, 128, 3, 2, 0), NB_VJP(128, 4, 128, 3, 4, 0), NB_VJP(256, 2, 64, 4, 2, 0),
-    NB_VJP(256, 2, 32, 4, 2, 0),
+    NB_VJP_M(256, 2, 128, 3, 2, 0, 2), NB_VJP_M(256, 2, 128, 3, 4, 0, 2), NB_VJP(512, 2, 128, 3, 2, 0),
+    NB_VJP_M(128, 2, 128, 3, 2, 0, 4), NB_VJP_M(256, 2, 256, 3, 2, 0, 2), NB_VJP(64, 4, 128, 3, 2, 0),
+    NB_VJP(128, 4, 128, 3, 2, 0), NB_VJP(128, 4, 128, 3, 4, 0), NB_VJP_M(256, 2, 64, 4, 2, 0, 2),
+    NB_VJP_M(256, 2, 32, 4, 2, 0, 2), NB_VJP(128, 4, 64, 4, 4, 0), NB_VJP(128, 4, 128, 4, 4, 0),
+    NB_VJP(128, 4, 64, 4, 2, 0),
 };
 #undef NB_VJP
 #undef NB_VJP_M
 constexpr int kVjpCount = (int)(sizeof(kVjp) / sizeof(kVjp[0]));
-// Built-in shapes by size (GB300 sweep, G-pairs/s): 64-particle j-tiles below
-// 2^15 (N = 16384: 936 against 912 for 128-particle tiles; the finer
-// (i-block, j-tile) units balance the persistent split), 256-particle tiles
-// from there (N = 65536: 1015 against 982). Shapes that force more resident
-// warps per SM (minblocks 3 or 6) spilled and ran 8-11% slower.
-constexpr int kVjpSmall = 8, kVjpLarge = 4;
+// Built-in shapes by size (GB300 sweep, G-pairs/s): two packed pairs per
+// thread in 128-thread CTAs (two per SM), 64-particle j-tiles below 2^15 (N =
+// 16384: 977 against 964 for 128-particle tiles, whose fewer (i-block,
+// j-tile) units balance the persistent split less evenly; one pair per
+// thread in 256-thread CTAs: 887), 128-particle tiles from there (N = 65536:
+// 1027 against 1000). Two pairs per thread took the lead once the diagonal
+// tiles ran unrolled in their lane-diagonal form (before: 916 / 1003, with
+// one pair per thread at 936 / 1015 the best). Shapes that force more
+// resident warps per SM (minblocks 3 or 6) spilled and ran 8-11% slower.
+constexpr int kVjpSmall = 10, kVjpLarge = 7;
 
 const VjpVariant &vjp_variant(nb_ctx *ctx, int64_t n) {
     const int k = ctx_ext(ctx).vjp_idx;
