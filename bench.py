@@ -490,9 +490,20 @@ def extra_adjoint(nb, ctx, dev, torch, plain_rate, oracle_ref=False):
     for _ in range(reps):
         nb.nb_force(ctx, x, mt, n, eps, a, p)
     f1.record()
+    # The trajectory adjoint's case: no upstream gradient on p (26 instead of
+    # 29 FP32 operations per pair).
+    for _ in range(3):
+        nb.nb_force_vjp(ctx, x, mt, n, eps, ga, None, gx, gm)
+    g0, g1 = _events(torch)
+    g0.record()
+    for _ in range(reps):
+        nb.nb_force_vjp(ctx, x, mt, n, eps, ga, None, gx, gm)
+    g1.record()
+    nb.nb_force_vjp(ctx, x, mt, n, eps, ga, gp, gx, gm)  # gx, gm with gp again (oracle check)
     nb.nb_synchronize(ctx)
     vjp_ms = e0.elapsed_time(e1) / reps
     fwd_ms = f0.elapsed_time(f1) / reps
+    vjp_nogp_ms = g0.elapsed_time(g1) / reps
     xt = torch.from_numpy(x0.copy()).to(dev).requires_grad_(True)
     vt = torch.from_numpy(v0.copy()).to(dev).requires_grad_(True)
     mg = torch.from_numpy(m.astype(np.float32)).to(dev).requires_grad_(True)
@@ -510,6 +521,8 @@ def extra_adjoint(nb, ctx, dev, torch, plain_rate, oracle_ref=False):
     traj_s = times[-1]
     out = {"workload": "plummer16384_adjoint64", "n": n,
            "vjp_ms": vjp_ms, "vjp_gpair_s": n * n / (vjp_ms * 1e-3) / 1e9,
+           "vjp_without_gp_ms": vjp_nogp_ms,
+           "vjp_without_gp_gpair_s": n * n / (vjp_nogp_ms * 1e-3) / 1e9,
            "forward_ms_same_n": fwd_ms,
            "vjp_fraction_of_plain_rate": (n * n / (vjp_ms * 1e-3) / 1e9) / plain_rate,
            "trajectory_grad_s": traj_s, "trajectory_grad_first_s": times[0]}
