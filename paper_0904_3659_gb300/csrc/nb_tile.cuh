@@ -132,7 +132,8 @@ __device__ __forceinline__ void tile_pass_diag32(int k, int lane, const JPart *_
 // the exact difference (up to the remainders' own rounding, far below it),
 // so close pairs keep their relative accuracy wherever they sit. 6 FP32
 // operations per pair more than tile_pass (19, or 18 without the potential).
-template <int P, int JT, int UNR, bool DIAG, bool POT>
+// DK >= 0: the lane-diagonal form, as for tile_pass.
+template <int P, int JT, int UNR, bool DIAG, bool POT, int DK = -1>
 __device__ __forceinline__ void tile_pass_hl(const JPart *__restrict__ T, const float2 (&xi)[P],
                                              const float2 (&yi)[P], const float2 (&zi)[P],
                                              const float2 (&lxi)[P], const float2 (&lyi)[P],
@@ -159,7 +160,13 @@ __device__ __forceinline__ void tile_pass_hl(const JPart *__restrict__ T, const 
             s = fma2(dz, dz, s);
             const float2 u = make_float2(rsqrt_sfu(s.x), rsqrt_sfu(s.y));
             float2 hm = hmj;
-            if (DIAG) {
+            if constexpr (DIAG && DK >= 0) {
+                static_assert(JT == 32 && DK < 2 * P, "the lane-diagonal form needs 32-particle tiles");
+                if (q == DK / 2 && jj == self0[0]) {
+                    if (DK % 2 == 0) hm.x = 0.f;
+                    else hm.y = 0.f;
+                }
+            } else if constexpr (DIAG) {
                 if (jj == self0[q]) hm.x = 0.f;
                 if (jj == self1[q]) hm.y = 0.f;
             }
