@@ -1240,6 +1240,7 @@ static const PairVariant kNoPot[] = {
     NB_VARIANT_NP(256, 4, 256, 3, 4, 1, 0, 0, 63, false, false, true),
     NB_VARIANT_NP(128, 12, 256, 3, 4, 1, 0, 1, 63, false, false, true),
     NB_VARIANT_NP(256, 4, 1024, 3, 4, 1, 0, 0, 63, true, false, true),
+    NB_VARIANT_NP(256, 4, 512, 3, 4, 1, 0, 0, 63, false, false, true),
 };
 static_assert(kDefaultRefine == 0, "the no-potential and HL shapes have no Newton step");
 #undef NB_VARIANT
@@ -1288,16 +1289,17 @@ static int pair_variant_index(bool comp, const nb_tile &t) {
 // the work cannot fill 152 SMs with large i-blocks, then 4 i per thread in
 // 256-thread CTAs. From N = 2^17 on, plain mode takes 1024-particle tiles
 // with the Kahan running sum (N = 2^20: 2639 against 2572 G-int/s for the
-// plain running sum at the same shape); below, 256-particle tiles, whose
-// no-potential twin runs the N = 2^16 leap-frog 0.6% faster than the Kahan
-// shape's (N = 2^16 with the potential: 2491 against 2594, which the tuner
+// plain running sum at the same shape); from 2^15, 512-particle tiles, whose
+// no-potential twin runs the N = 2^16 leap-frog 0.8% faster than 256-particle
+// tiles and 1.4% faster than the Kahan shape's (N = 2^16 with the potential:
+// 2511 against 2491 for 256 and 2594 for the Kahan shape, which the tuner
 // picks). From N = 2^15 on, compensated mode takes 512-particle tiles (N =
 // 2^16, 2^20: 2576, 2621 against 2541, 2585 for 256).
 int pair_default_unfused_index(bool comp, int64_t n) {
     constexpr int R = kDefaultRefine;
     static const nb_tile shapes[2][4] = {
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {64, 4, 128, 4, 4, 1, 0, 0, 63, R},
-         {256, 4, 256, 3, 4, 1, 0, 0, 63, R}, {256, 4, 1024, 3, 4, 1, 0, 0, 63, R}},
+         {256, 4, 512, 3, 4, 1, 0, 0, 63, R}, {256, 4, 1024, 3, 4, 1, 0, 0, 63, R}},
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R},
          {256, 4, 512, 3, 4, 1, 0, 0, 63, R}, {256, 4, 512, 3, 4, 1, 0, 0, 63, R}}};
     static const int idx[2][4] = {
