@@ -236,7 +236,7 @@ ClusterLoad cluster_load(nb_ctx *ctx, const PairVariant &v, int64_t n) {
 // gives the busiest SM less work, or as much work with clusters that fit
 // where the built-in one's do not. At N = 7168 two CTAs per SM take clusters
 // of 5 where one CTA per SM allows only 2 (29.8 against 32.2 us per call);
-// at N = 1024 clusters of 8 CTAs fit only at two per SM (5.4 against 7.5 us).
+// at N = 1024 clusters of 8 CTAs fit only at two per SM (5.7 against 7.5 us).
 int default_index(nb_ctx *ctx, int64_t n, bool comp) {
     const int k = pair_default_index(comp, n);
     const PairVariant &v = *pair_variant(comp, k);

@@ -1124,8 +1124,8 @@ constexpr size_t pair_smem() {
 // per SM: 2 holds the registers to 128 per thread; 1 requests
 // kClusterOneSmSmem, so that exactly one CTA runs per SM whatever the
 // register count (at N = 4096, 32 clusters of 4 CTAs on 128 SMs: 11.0 us per
-// call, against 11.3 us when the 128-register kernel put two CTAs on some
-// SMs and none on others).
+// call, against 11.3 us when the 128-register kernel ran two CTAs per SM in
+// clusters of 8: 256 CTAs, two on 104 SMs).
 constexpr size_t kClusterOneSmSmem = 120 * 1024;
 static_assert(kClusterOneSmSmem >= kFusedJmax * sizeof(JPart) + 2 * kClusterSlots * sizeof(float4) &&
                   kClusterOneSmSmem <= 227 * 1024,
