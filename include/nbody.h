@@ -203,7 +203,10 @@ nb_status nb_reserve(nb_ctx *ctx, int64_t n, nb_mode mode);
  * chunk of at most a quarter of its j-range), taken from a device queue by
  * the warps of one persistent launch, largest clusters first; each item is
  * summed by one warp in a fixed order and the chunks are added in chunk
- * order (bit-reproducible).
+ * order (bit-reproducible). The item list is kept in the context and reused
+ * by the next call (batched force or batched leap-frog) while n_clusters,
+ * n_total and the values of offsets and eps stay the same, which the device
+ * checks on every call; any change makes a new list.
  */
 nb_status nb_force_batched(nb_ctx *ctx, const float *x, const float *m, const int64_t *offsets,
                            int64_t n_clusters, int64_t n_total, const float *eps,
