@@ -678,6 +678,42 @@ __global__ void batch_kick_drift_kernel(double *__restrict__ x, double *__restri
     x[k] = x[k] + dt * vc;           // Eq. (2)
 }
 
+// Plain mode: the same kick and drift for the particles of one block of
+// kClusterPad padded rows, fused with the packing of the moved positions
+// (batch_pack_kernel<double>'s records), so the positions are read once.
+__global__ void __launch_bounds__(kClusterPad) batch_kick_drift_pack_kernel(
+    double *__restrict__ x, double *__restrict__ v, const float *__restrict__ a,
+    const float *__restrict__ m, const int64_t *__restrict__ off, const int64_t *__restrict__ poff,
+    int64_t C, double dt, int kick_back, JPart *__restrict__ jp) {
+    const int64_t s = (int64_t)blockIdx.x * kClusterPad;
+    if (s >= poff[C]) return;
+    const int64_t c = padded_cluster(poff, C, s);
+    const int64_t li = s - poff[c] + threadIdx.x, o = off[c], nc = off[c + 1] - o;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (li < nc) {
+        const int64_t i = o + li;
+        const double h = 0.5 * dt;
+        float q[3];
+        for (int k = 0; k < 3; ++k) {
+            const int64_t e = 3 * i + k;
+            const double g = -(double)a[e];
+            double vc = v[e];
+            if (kick_back) vc = vc + h * g;  // Eq. (3) of the previous step
+            vc = vc + h * g;                 // Eq. (1)
+            v[e] = vc;
+            const double xn = x[e] + dt * vc;  // Eq. (2)
+            x[e] = xn;
+            q[k] = (float)xn;
+        }
+        const float hm = -0.5f * m[i];
+        lo = make_float4(-q[0], -q[0], -q[1], -q[1]);
+        hi = make_float4(-q[2], -q[2], hm, hm);
+    }
+    float4 *dst = reinterpret_cast<float4 *>(jp + s + threadIdx.x);
+    dst[0] = lo;
+    dst[1] = hi;
+}
+
 __global__ void batch_kick_kernel(double *__restrict__ v, const float *__restrict__ a, int64_t n,
                                   double dt) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -944,6 +980,13 @@ nb_status nb_leapfrog_batched_step(nb_ctx *ctx, double *x, double *v, const floa
         return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);
     };
     auto step = [&](int kick_back) -> nb_status {
+        if (!hl) {  // kick, drift and pack in one pass, then the force
+            batch_kick_drift_pack_kernel<<<npack, kClusterPad, 0, s>>>(x, v, a, m, offsets, poff, n_clusters,
+                                                                       dt, kick_back, jp);
+            cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) return cuda_fail(ctx, le, "leap-frog update launch");
+            return batch_pair(ctx, offsets, n_clusters, eps, a, p, h, s);
+        }
         batch_kick_drift_kernel<<<nb3, 256, 0, s>>>(x, v, a, n_total, dt, kick_back);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(ctx, le, "leap-frog update launch");
