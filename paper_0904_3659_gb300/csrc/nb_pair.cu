@@ -1194,6 +1194,7 @@ static const PairVariant kPlain[] = {
 static const PairVariant kComp[] = {
     NB_VARIANT(128, 6, 256, 3, 8, 1, 0, 1, 63, 0, true),
     NB_VARIANT(256, 4, 512, 3, 4, 1, 0, 0, 63, 0, true),
+    NB_VARIANT(256, 4, 768, 3, 4, 1, 0, 0, 63, 0, true),
     NB_VARIANT(128, 8, 256, 3, 8, 1, 1, 1, 63, 0, true),
     NB_VARIANT(128, 12, 256, 3, 4, 1, 0, 1, 63, 0, true),
     NB_VARIANT(256, 4, 256, 3, 4, 1, 0, 0, 63, 0, true),
@@ -1293,15 +1294,17 @@ static int pair_variant_index(bool comp, const nb_tile &t) {
 // no-potential twin runs the N = 2^16 leap-frog 0.8% faster than 256-particle
 // tiles and 1.4% faster than the Kahan shape's (N = 2^16 with the potential:
 // 2511 against 2491 for 256 and 2594 for the Kahan shape, which the tuner
-// picks). From N = 2^15 on, compensated mode takes 512-particle tiles (N =
-// 2^16, 2^20: 2576, 2621 against 2541, 2585 for 256).
+// picks). Compensated mode takes 512-particle tiles from N = 2^15 (N = 2^16:
+// 2574 against 2539 for 256 and 2507 for 768) and 768-particle tiles from
+// 2^17 (N = 2^20: 2629 against 2618 for 512 and 2582 for 256; every shape
+// stays within the mode's 1e-6, the 1536-particle tiles did not).
 int pair_default_unfused_index(bool comp, int64_t n) {
     constexpr int R = kDefaultRefine;
     static const nb_tile shapes[2][4] = {
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {64, 4, 128, 4, 4, 1, 0, 0, 63, R},
          {256, 4, 512, 3, 4, 1, 0, 0, 63, R}, {256, 4, 1024, 3, 4, 1, 0, 0, 63, R}},
         {{256, 2, 128, 4, 4, 1, 0, 0, 63, R}, {256, 4, 256, 3, 4, 1, 0, 0, 63, R},
-         {256, 4, 512, 3, 4, 1, 0, 0, 63, R}, {256, 4, 512, 3, 4, 1, 0, 0, 63, R}}};
+         {256, 4, 512, 3, 4, 1, 0, 0, 63, R}, {256, 4, 768, 3, 4, 1, 0, 0, 63, R}}};
     static const int idx[2][4] = {
         {pair_variant_index(false, shapes[0][0]), pair_variant_index(false, shapes[0][1]),
          pair_variant_index(false, shapes[0][2]), pair_variant_index(false, shapes[0][3])},
