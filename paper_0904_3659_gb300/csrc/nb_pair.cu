@@ -451,17 +451,6 @@ __device__ __forceinline__ void pack_block(const float *__restrict__ x, const fl
     }
 }
 
-// Programmatic dependent launch of the single-launch kernels: they are
-// launched with programmatic stream serialization, so the next launch on the
-// stream can be scheduled while this one runs; a kernel waits for its
-// predecessor's completion (and memory) before it reads anything, and
-// releases its own dependents at once (they too wait for its completion
-// before reading). Without such a launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_wait_then_release() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 template <int WARPS, int IPT, int JT, int UNR, int MINB, bool NEWTON, bool COMP>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fused_kernel(const FusedArgs args) {
     static_assert(IPT % 2 == 0, "i-particles are processed in packed pairs");

@@ -56,6 +56,7 @@ static_assert(sizeof(VPart) == 64, "VPart must be 64 bytes");
 __global__ void vjp_pack_kernel(const float *__restrict__ x, const float *__restrict__ m,
                                 const float *__restrict__ ga, const float *__restrict__ gp,
                                 int64_t n, int64_t npad, VPart *__restrict__ vp) {
+    pdl_wait_then_release();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= npad) return;
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(THREADS, MINB) vjp_kernel(const VjpArgs args) 
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * TILE_BYTES +
                                                   (ACCS ? (size_t)P * 8 * THREADS * sizeof(float2) : 0));
 
+    pdl_wait_then_release();
     const int tid = threadIdx.x;
     const int64_t c = blockIdx.x;
     const int64_t u0 = c * args.units / args.grid;
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(THREADS, MINB) vjp_kernel(const VjpArgs args) 
 // Combine the per-segment sums of each i (CTA order) and form gx, gm.
 __global__ void vjp_combine_kernel(const VjpArgs A, int ib, float *__restrict__ gx,
                                    float *__restrict__ gm) {
+    pdl_wait_then_release();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     const int64_t b = i / ib, w = i - b * ib;
@@ -411,7 +414,7 @@ struct VjpVariant {
 
 template <int T, int I, int J, int S, int U, int A, bool G, int M>
 void launch_vjp(const VjpArgs &a, int grid, size_t smem, cudaStream_t st) {
-    vjp_kernel<T, I, J, S, U, A, G, M><<<grid, T, smem, st>>>(a);
+    launch_with_pdl(vjp_kernel<T, I, J, S, U, A, G, M>, dim3(grid), dim3(T), smem, st, a);
 }
 
 template <int T, int I, int J, int S, int A>
@@ -485,8 +488,11 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
         e = ensure_buffer(&es.buf[V_PART], &es.cap[V_PART], plan.partial_bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation (vjp)");
     VPart *vp = static_cast<VPart *>(es.buf[V_VP]);
-    vjp_pack_kernel<<<(unsigned)((plan.npad + 255) / 256), 256, 0, s>>>(x, m, ga, gp, n, plan.npad, vp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp pack launch");
+    // The three launches go out with programmatic dependent launch: each is
+    // scheduled while its predecessor runs and waits for its results.
+    e = launch_with_pdl(vjp_pack_kernel, dim3((unsigned)((plan.npad + 255) / 256)), dim3(256), 0, s, x, m, ga,
+                        gp, n, plan.npad, vp);
+    if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp pack launch");
 
     VjpArgs A{};
     A.vp = vp;
@@ -510,8 +516,8 @@ extern "C" nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, i
         vv.launch[with_gp](A, plan.grid, vv.smem, s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp kernel launch");
-    vjp_combine_kernel<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(A, plan.ib, gx, gm);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp combine launch");
+    e = launch_with_pdl(vjp_combine_kernel, dim3((unsigned)((n + 63) / 64)), dim3(64), 0, s, A, plan.ib, gx, gm);
+    if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "vjp combine launch");
     return NB_OK;
 }
 
