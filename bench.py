@@ -491,7 +491,7 @@ def extra_adjoint(nb, ctx, dev, torch, plain_rate, oracle_ref=False):
         nb.nb_force(ctx, x, mt, n, eps, a, p)
     f1.record()
     # The trajectory adjoint's case: no upstream gradient on p (26 instead of
-    # 29 FP32 operations per pair).
+    # 28 FP32 operations per pair).
     for _ in range(3):
         nb.nb_force_vjp(ctx, x, mt, n, eps, ga, None, gx, gm)
     g0, g1 = _events(torch)
@@ -1025,19 +1025,23 @@ def run_sweep(args):
             reps = 3 if n >= 1 << 19 else (10 if n >= 1 << 16 else 50)
             for t in nb.nb_list_vjp_tiles():
                 nb.nb_set_vjp_tile(ctx, t)
-                for _ in range(2):
-                    nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, gp, gx, gm)
-                nb.nb_synchronize(ctx)
-                nb.nb_timing_enable(ctx, True)
-                nb.nb_timing_reset(ctx)
-                for _ in range(reps):
-                    nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, gp, gx, gm)
-                nb.nb_synchronize(ctx)
-                ms, cnt = nb.nb_timing_read(ctx, nb.KERNEL_VJP)
-                nb.nb_timing_enable(ctx, False)
-                print(json.dumps({"n": n, "kernel": "vjp", "tile": list(t.as_tuple()),
-                                  "vjp_ms": ms / cnt,
-                                  "gpair_s": n * n / (ms / cnt * 1e-3) / 1e9}), flush=True)
+                line = {"n": n, "kernel": "vjp", "tile": list(t.as_tuple())}
+                # With the upstream gradient on p, then without it (the
+                # trajectory adjoint's case, a kernel of its own).
+                for key, g in (("", gp), ("_without_gp", None)):
+                    for _ in range(2):
+                        nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, g, gx, gm)
+                    nb.nb_synchronize(ctx)
+                    nb.nb_timing_enable(ctx, True)
+                    nb.nb_timing_reset(ctx)
+                    for _ in range(reps):
+                        nb.nb_force_vjp(ctx, x, mt, n, 1.0 / 64, ga, g, gx, gm)
+                    nb.nb_synchronize(ctx)
+                    ms, cnt = nb.nb_timing_read(ctx, nb.KERNEL_VJP)
+                    nb.nb_timing_enable(ctx, False)
+                    line["vjp_ms" + key] = ms / cnt
+                    line["gpair_s" + key] = n * n / (ms / cnt * 1e-3) / 1e9
+                print(json.dumps(line), flush=True)
             nb.nb_set_vjp_tile(ctx, None)
         return
     for n in sizes:

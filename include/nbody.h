@@ -302,7 +302,7 @@ nb_status nb_energy(nb_ctx *ctx, const double *x, const double *v, const float *
  * on a and gp [n] on p, the gradient of L = sum_i ga_i . a_i + gp_i p_i with
  * respect to the positions, gx [n][3], and masses, gm [n]. All FP32 device
  * arrays; gp may be NULL (no upstream gradient on p: a kernel without its
- * terms runs, 26 instead of 29 FP32 operations per pair). Computed as one
+ * terms runs, 26 instead of 28 FP32 operations per pair). Computed as one
  * gather pass over all pairs (no atomics), so the result is reproducible.
  * Asynchronous.
  */
@@ -310,11 +310,12 @@ nb_status nb_force_vjp(nb_ctx *ctx, const float *x, const float *m, int64_t n, f
                        const float *ga, const float *gp, float *gx, float *gm, void *stream);
 
 /* Shape of nb_force_vjp's pair kernel (nb_tile fields threads, ipt, jtile,
- * stages, unroll, minblocks, sums_in_smem; the others as listed): force one
- * of the compiled shapes listed by nb_list_vjp_tiles (NULL restores the
- * built-in choice by size), read the shape nb_force_vjp uses at size n, list
- * the compiled shapes (up to `cap` written to out, which may be NULL; the
- * total in *count). */
+ * stages, unroll, minblocks, release, sums_in_smem; the others as listed):
+ * force one of the compiled shapes listed by nb_list_vjp_tiles (NULL
+ * restores the built-in choice, by size and by whether gp is NULL), read the
+ * shape nb_force_vjp uses at size n for a call with gp non-NULL, list the
+ * compiled shapes (up to `cap` written to out, which may be NULL; the total
+ * in *count). */
 nb_status nb_set_vjp_tile(nb_ctx *ctx, const nb_tile *tile);
 nb_status nb_get_vjp_tile(nb_ctx *ctx, int64_t n, nb_tile *out);
 nb_status nb_list_vjp_tiles(nb_tile *out, int cap, int *count);
@@ -395,8 +396,9 @@ nb_status nb_timing_enable(nb_ctx *ctx, int on);
 nb_status nb_timing_read(nb_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
 nb_status nb_timing_reset(nb_ctx *ctx);
 
-/* Test hook for the bounded-wait path: with unit >= 0 the pair kernel's
- * producer does not issue the copy of work unit `unit`, so the consumers'
+/* Test hook for the bounded-wait path: with unit >= 0 the producer of the
+ * pair kernel (and of the adjoint kernel of nb_force_vjp) does not issue the
+ * copy of work unit `unit`, so the consumers'
  * bounded wait runs out, the kernel records a timeout and returns, and the
  * next nb_synchronize reports NB_ERR_TIMEOUT. In the cluster form of the
  * single-launch kernel (nb_tile.fused = 3) CTA `unit` does not send its

@@ -131,6 +131,7 @@ bool ctx_set_timing(nb_ctx *ctx, bool on) {
     return prev;
 }
 uint64_t ctx_wait_ns(const nb_ctx *ctx) { return ctx->wait_ns; }
+int64_t ctx_fault_unit(const nb_ctx *ctx) { return ctx->fault_unit; }
 
 static_assert(ExtState::kSlots == SLOT_COUNT, "one buffer per slot id");
 

@@ -68,6 +68,7 @@ int ctx_device(const nb_ctx *ctx);
 int ctx_sm_count(const nb_ctx *ctx);
 int *ctx_err_word(nb_ctx *ctx);
 uint64_t ctx_wait_ns(const nb_ctx *ctx);
+int64_t ctx_fault_unit(const nb_ctx *ctx);
 ExtState &ctx_ext(nb_ctx *ctx);
 // Turn per-kernel event timing on or off; returns the previous setting.
 bool ctx_set_timing(nb_ctx *ctx, bool on);

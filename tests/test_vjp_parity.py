@@ -134,6 +134,45 @@ def test_every_vjp_shape(nb, ctx, oracle_mod):
         nb.nb_set_vjp_tile(ctx, None)
 
 
+@pytest.mark.parametrize("release", [0, 1])
+def test_vjp_bounded_wait_reports_timeout_and_context_survives(nb, ctx, oracle_mod, release):
+    # The adjoint kernel's producer skips the copy of one work unit, so the
+    # consumers' bounded wait (0.2 s) runs out; the kernel records a timeout
+    # and returns, nb_synchronize reports it, and the next call on the same
+    # context is correct. Both stage-release schemes (a barrier per tile; the
+    # last warp out of a stage refills it).
+    n = 4096
+    x, _, m = workloads.plummer(n, seed=81)
+    x32, m32 = x.astype(np.float32), m.astype(np.float32)
+    rng = np.random.default_rng(82)
+    ga = rng.normal(size=(n, 3)).astype(np.float32)
+    gp = rng.normal(size=n).astype(np.float32)
+    eps = np.float32(1.0 / 64)
+    tile = [t for t in nb.nb_list_vjp_tiles() if t.release == release][0]
+    nb.nb_set_vjp_tile(ctx, tile)
+    try:
+        nb.nb_debug_set_fault(ctx, 3, 200_000_000)
+        try:
+            import torch
+            dev = torch.device("cuda:0")
+            t = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).to(dev)
+            gx = torch.empty((n, 3), device=dev)
+            gm = torch.empty(n, device=dev)
+            nb.nb_force_vjp(ctx, t(x32), t(m32), n, eps, t(ga), t(gp), gx, gm)
+            with pytest.raises(nb.NBError) as e:
+                nb.nb_synchronize(ctx)
+            assert e.value.status == nb.NB_ERR_TIMEOUT
+        finally:
+            nb.nb_debug_set_fault(ctx, -1, 0)
+        gx, gm = gpu_vjp(nb, ctx, x32, m32, eps, ga, gp)
+    finally:
+        nb.nb_set_vjp_tile(ctx, None)
+    rgx, rgm = oracle_mod.force_vjp(x32, m32, eps, ga, gp)
+    sx, sm = vjp_term_scales(x32, m32, eps, ga, gp)
+    assert rel_to_scale(gx, rgx, sx) <= 1e-5
+    assert rel_to_scale(gm, rgm, sm) <= 1e-5
+
+
 def test_vjp_without_potential_gradient(nb, ctx, oracle_mod):
     # gp = NULL (no upstream gradient on p) runs the kernel without the p
     # terms: it must match the oracle with gp = 0, for every compiled shape.
