@@ -415,6 +415,7 @@ def nb_set_vjp_tile(ctx, tile) -> None:
 
 
 def nb_get_vjp_tile(ctx, n=1 << 20) -> nb_tile:
+    """The shape nb_force_vjp uses at size n for a call with gp given."""
     t = nb_tile()
     _check(ctx, library().nb_get_vjp_tile(ctx.handle, int(n), ctypes.byref(t)))
     return t
