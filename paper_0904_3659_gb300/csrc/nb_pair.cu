@@ -1305,16 +1305,20 @@ int pair_default_unfused_index(bool comp, int64_t n) {
 }
 
 // Single-launch shapes by size (GB300, whole calls, plain / compensated):
-// the cluster form below kChunkedMaxN, 2 i per lane below kClusterWideMinN
+// the cluster form up to kClusterMaxN, 2 i per lane below kClusterWideMinN
 // (N = 2048: 5.8 / 5.7 us against 7.1 / 7.5 with 4) and 4 from there (N =
 // 3072: 8.6 / 9.2 us against 9.2 / 9.9 with 2, whose clusters of 3 do not
 // all fit; N = 4096: 11.0 / 11.7 against 12.6 / 13.3 for the chunked form and
-// 30.7 for pack + pair + combine), the stream-K form from there to
-// kFusedMaxN (N = 12288: 73.8 / 77.5 us against 92.2 / 94.4 us for the best
-// packed shapes; N = 16384: 129.0 / 133.5 against 137.2 / 141.3 us), the
-// packed shapes above (N = 24576: stream-K 279.0 / 290.5 us against 280.5 /
-// 280.7).
-constexpr int64_t kChunkedMaxN = (int64_t)1 << 13;
+// 30.7 for pack + pair + combine; N = 9216: 40.4 / 41.8 against 44.4 / 45.4
+// for the stream-K form). kClusterMaxN is 76 i-blocks of 128: the most
+// clusters of two that fit at once at one CTA per SM (N = 9728: 42.6 / 43.9
+// against 45.9 / 46.7 for stream-K; at N = 10240 the 80 clusters do not fit
+// and stream-K wins, 53.5 / 54.6 against 59.2 / 61.0). The stream-K form from
+// there to kFusedMaxN (N = 12288: 73.8 / 77.5 us against 92.2 / 94.4 us for
+// the best packed shapes; N = 16384: 129.0 / 133.5 against 137.2 / 141.3
+// us), the packed shapes above (N = 24576: stream-K 279.0 / 290.5 us against
+// 280.5 / 280.7).
+constexpr int64_t kClusterMaxN = (int64_t)76 * 128;
 constexpr int64_t kClusterWideMinN = (int64_t)3 << 10;
 constexpr int64_t kFusedMaxN = (int64_t)3 << 13;
 
@@ -1323,7 +1327,7 @@ bool fused_candidate(int64_t n) { return n < (int64_t)1 << 16; }
 int pair_default_index(bool comp, int64_t n) {
     if (n >= kFusedMaxN) return pair_default_unfused_index(comp, n);
     constexpr int R = kDefaultRefine;
-    // Below kChunkedMaxN the cluster form (the chunked split, partials met in
+    // Up to kClusterMaxN the cluster form (the chunked split, partials met in
     // distributed shared memory; it runs as the chunked form when its
     // clusters do not fit at once), one CTA per SM: 2 i per lane below
     // kClusterWideMinN, 4 from there.
@@ -1333,7 +1337,7 @@ int pair_default_index(bool comp, int64_t n) {
     static const int idx[3][2] = {{pair_variant_index(false, cl2), pair_variant_index(true, cl2)},
                                   {pair_variant_index(false, cl4), pair_variant_index(true, cl4)},
                                   {pair_variant_index(false, streamk), pair_variant_index(true, streamk)}};
-    const int cls = n < kClusterWideMinN ? 0 : n < kChunkedMaxN ? 1 : 2;
+    const int cls = n < kClusterWideMinN ? 0 : n <= kClusterMaxN ? 1 : 2;
     const int k = idx[cls][comp ? 1 : 0];
     return k >= 0 ? k : pair_default_unfused_index(comp, n);
 }

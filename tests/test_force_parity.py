@@ -117,13 +117,14 @@ def test_default_shapes_skip_newton_step(nb, ctx):
 
 
 def test_default_path_by_size(nb):
-    # Built-in choice without tuning: the cluster single-launch shape below
-    # 8192, the stream-K form up to 24576, pack -> pair -> combine above.
+    # Built-in choice without tuning: the cluster single-launch shape up to
+    # 9728 (76 clusters of two), the stream-K form up to 24576, pack -> pair
+    # -> combine above.
     fresh = nb.Context(0)
     try:
         for mode in (0, 1):
-            for n, fused in ((1, 3), (4096, 3), (8191, 3), (8192, 2), (16384, 2), (24575, 2),
-                             (24576, 0), (1 << 20, 0)):
+            for n, fused in ((1, 3), (4096, 3), (8192, 3), (9728, 3), (9729, 2), (16384, 2),
+                             (24575, 2), (24576, 0), (1 << 20, 0)):
                 assert nb.nb_get_tile(fresh, n, mode).fused == fused, (mode, n)
     finally:
         fresh.close()
@@ -163,10 +164,10 @@ def test_fused_shapes(nb, ctx, oracle_mod, mode):
     eps = np.float32(1.0 / 64)
     cases = []
     # 20000: a stream-K CTA's range can touch three i-blocks (and the cluster
-    # form falls to one CTA per cluster); 4096, 7168 and 8191: the chunked and
+    # form falls to one CTA per cluster); 4096, 7168 and 9728: the chunked and
     # cluster forms' workload, a size where two CTAs per SM take larger
-    # clusters than one, and their largest built-in size.
-    for n in (1, 200, 3001, 4096, 7168, 8191, 9000, 20000):
+    # clusters than one, and their largest built-in size (76 clusters of two).
+    for n in (1, 200, 3001, 4096, 7168, 8191, 9000, 9728, 20000):
         x32, m32 = plummer32(n, seed=100 + n)
         cases.append((n, x32, m32, oracle_mod.force(x32, m32, eps)))
     try:
