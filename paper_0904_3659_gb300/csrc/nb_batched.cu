@@ -367,6 +367,7 @@ struct BatchArgs {
 
 struct StageMeta {
     int item, cluster, iblock, jt, end;
+    int len;  // particles copied into the stage: JT, or the cluster's last, shorter tile
 };
 
 // HL: the particles are HL records (two JParts each, batch_pack_hl_kernel)
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
 
     // Producer state (lane 0): walks the (item, j-tile) stream, popping items.
     int p_item = -1, p_cluster = 0, p_b = 0, p_jt = 0, p_ntiles = 0, p_done = 0;
-    int64_t p_base = 0;
+    int64_t p_base = 0, p_nc = 0;
     const int nitems = *A.nitems;
     auto produce = [&](int kk) {
         const int s = kk % STAGES;
@@ -424,18 +425,24 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                 p_cluster = w.x;
                 p_b = w.y;
                 p_base = A.poff[w.x];
+                p_nc = A.off[w.x + 1] - A.off[w.x];
                 const int ntiles = (int)((A.poff[w.x + 1] - p_base) / JT);
                 // chunk w.z of w.w: tiles [w.z*ntiles/w.w, (w.z+1)*ntiles/w.w)
                 p_jt = (int)((int64_t)w.z * ntiles / w.w);
                 p_ntiles = (int)((int64_t)(w.z + 1) * ntiles / w.w);
             }
         }
+        // The cluster's last tile stops at its last particle, rounded up to a
+        // multiple of 32: the padding rows beyond add nothing (zero mass).
+        const int64_t rem = p_nc - (int64_t)p_jt * JT;
+        const int len = rem >= JT ? JT : rem > 0 ? (int)((rem + 31) & ~(int64_t)31) : 32;
         StageMeta mt;
         mt.end = p_done;
         mt.item = p_item;
         mt.cluster = p_cluster;
         mt.iblock = p_b;
         mt.jt = p_jt;
+        mt.len = len;
         meta[s] = mt;
         if (!p_done && !NB_IN(A.err, 11, p_base + (int64_t)(p_jt + 1) * JT <= A.cap_padded))
             p_done = 1;
@@ -446,8 +453,9 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                          : "memory");
         } else {
             issued_at[s] = kk;
-            mbar_arrive_expect_tx(&full[s], TILE_BYTES);
-            bulk_g2s(tiles + (size_t)s * JT * RS, A.jp + (p_base + (int64_t)p_jt * JT) * RS, TILE_BYTES,
+            const uint32_t bytes = (uint32_t)len * RS * (uint32_t)sizeof(JPart);
+            mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_g2s(tiles + (size_t)s * JT * RS, A.jp + (p_base + (int64_t)p_jt * JT) * RS, bytes,
                      &full[s]);
             ++p_jt;
         }
@@ -543,20 +551,30 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                 // compensated ones gained 2-3%.)
 #pragma unroll
                 for (int q = 0; q < P; ++q) self0[q] = self1[q] = lane;
+                // Quarters past a short last tile hold only padding: skipped.
                 if constexpr (HL) {
                     tile_pass_hl<P, 32, 4, true, true, 0>(T, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0, self1);
-                    tile_pass_hl<P, 32, 4, true, true, 1>(T + 64, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
-                                                          self1);
-                    tile_pass_hl<P, 32, 4, true, true, 2>(T + 128, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
-                                                          self1);
-                    tile_pass_hl<P, 32, 4, true, true, 3>(T + 192, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
-                                                          self1);
+                    if (mt.len > 32)
+                        tile_pass_hl<P, 32, 4, true, true, 1>(T + 64, xi, yi, zi, lxi, lyi, lzi, acc, eps2,
+                                                              self0, self1);
+                    if (mt.len > 64)
+                        tile_pass_hl<P, 32, 4, true, true, 2>(T + 128, xi, yi, zi, lxi, lyi, lzi, acc, eps2,
+                                                              self0, self1);
+                    if (mt.len > 96)
+                        tile_pass_hl<P, 32, 4, true, true, 3>(T + 192, xi, yi, zi, lxi, lyi, lzi, acc, eps2,
+                                                              self0, self1);
                 } else {
                     constexpr bool NW = kDefaultRefine != 0;
                     tile_pass<P, 32, 4, true, kMixAll, NW, true, 0>(T, xi, yi, zi, acc, eps2, self0, self1);
-                    tile_pass<P, 32, 4, true, kMixAll, NW, true, 1>(T + 32, xi, yi, zi, acc, eps2, self0, self1);
-                    tile_pass<P, 32, 4, true, kMixAll, NW, true, 2>(T + 64, xi, yi, zi, acc, eps2, self0, self1);
-                    tile_pass<P, 32, 4, true, kMixAll, NW, true, 3>(T + 96, xi, yi, zi, acc, eps2, self0, self1);
+                    if (mt.len > 32)
+                        tile_pass<P, 32, 4, true, kMixAll, NW, true, 1>(T + 32, xi, yi, zi, acc, eps2, self0,
+                                                                        self1);
+                    if (mt.len > 64)
+                        tile_pass<P, 32, 4, true, kMixAll, NW, true, 2>(T + 64, xi, yi, zi, acc, eps2, self0,
+                                                                        self1);
+                    if (mt.len > 96)
+                        tile_pass<P, 32, 4, true, kMixAll, NW, true, 3>(T + 96, xi, yi, zi, acc, eps2, self0,
+                                                                        self1);
                 }
             } else {
 #pragma unroll
@@ -564,20 +582,48 @@ __global__ void __launch_bounds__(WARPS * 32) batched_pair_kernel(const BatchArg
                     self0[q] = ibase + (2 * q) * 32 + lane - jbase;
                     self1[q] = self0[q] + 32;
                 }
-                if constexpr (HL)
-                    tile_pass_hl<P, JT, 1, true, true>(T, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
-                                                       self1);
-                else
-                    tile_pass<P, JT, 1, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2,
-                                                                            self0, self1);
+                if (mt.len == JT) {
+                    if constexpr (HL)
+                        tile_pass_hl<P, JT, 1, true, true>(T, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
+                                                           self1);
+                    else
+                        tile_pass<P, JT, 1, true, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2,
+                                                                                self0, self1);
+                } else {
+                    // A short last tile, in 32-particle pieces (self indices
+                    // relative to each piece).
+                    for (int o = 0; o < mt.len; o += 32) {
+                        if constexpr (HL)
+                            tile_pass_hl<P, 32, 1, true, true>(T + o * RS, xi, yi, zi, lxi, lyi, lzi, acc, eps2,
+                                                               self0, self1);
+                        else
+                            tile_pass<P, 32, 1, true, kMixAll, kDefaultRefine != 0>(T + o, xi, yi, zi, acc,
+                                                                                    eps2, self0, self1);
+#pragma unroll
+                        for (int q = 0; q < P; ++q) {
+                            self0[q] -= 32;
+                            self1[q] -= 32;
+                        }
+                    }
+                }
             }
-        } else {
+        } else if (mt.len == JT) {
             if constexpr (HL)
                 tile_pass_hl<P, JT, 4, false, true>(T, xi, yi, zi, lxi, lyi, lzi, acc, eps2, self0,
                                                     self1);
             else
                 tile_pass<P, JT, 4, false, kMixAll, kDefaultRefine != 0>(T, xi, yi, zi, acc, eps2,
                                                                          self0, self1);
+        } else {
+            // A short last tile, in 32-particle pieces.
+            for (int o = 0; o < mt.len; o += 32) {
+                if constexpr (HL)
+                    tile_pass_hl<P, 32, 4, false, true>(T + o * RS, xi, yi, zi, lxi, lyi, lzi, acc, eps2,
+                                                        self0, self1);
+                else
+                    tile_pass<P, 32, 4, false, kMixAll, kDefaultRefine != 0>(T + o, xi, yi, zi, acc, eps2,
+                                                                             self0, self1);
+            }
         }
 #pragma unroll
         for (int q = 0; q < P; ++q)
