@@ -1309,7 +1309,7 @@ int pair_default_unfused_index(bool comp, int64_t n) {
 // (N = 2048: 5.8 / 5.7 us against 7.1 / 7.5 with 4) and 4 from there (N =
 // 3072: 8.6 / 9.2 us against 9.2 / 9.9 with 2, whose clusters of 3 do not
 // all fit; N = 4096: 11.0 / 11.7 against 12.6 / 13.3 for the chunked form and
-// 30.7 for pack + pair + combine; N = 9216: 40.4 / 41.8 against 44.4 / 45.4
+// 30.7 for pack + pair + combine; N = 9216: 40.7 / 41.8 against 44.4 / 45.4
 // for the stream-K form). kClusterMaxN is 76 i-blocks of 128: the most
 // clusters of two that fit at once at one CTA per SM (N = 9728: 42.6 / 43.9
 // against 45.9 / 46.7 for stream-K; at N = 10240 the 80 clusters do not fit
